@@ -1,0 +1,39 @@
+"""Write the shaped synthetic mechanisms to ``synth/data`` (TEST INFRASTRUCTURE).
+
+Run once: ``python -m oracle.make_inputs``.  Calls only ``synth`` (random
+draws) and ``oracle`` (shaping).  Prints the spectral radius of the analytic
+Jacobian at a few seeded states of each workload as a stiffness report.
+"""
+from __future__ import annotations
+
+import sys
+
+import numpy as np
+
+import synth
+from synth.configs import CONFIGS, save_mechanism
+
+from .mechgen import make_mechanism
+from .oracle import OracleMech
+
+
+def main(names=None):
+    for cname, cfg in CONFIGS.items():
+        if names and cname not in names:
+            continue
+        print(f"{cname}: {cfg['mech']}")
+        m = make_mechanism(cfg["n_species"], cfg["n_reactions"], cfg["n_thirdbody"], cfg["n_falloff"],
+                           cfg["elements"], cfg["mech_seed"])
+        path = save_mechanism(cfg["mech"], m)
+        print(f"  wrote {path}")
+        om = OracleMech(m)
+        rng = np.random.default_rng(7)
+        y, p = synth.draw_states(rng, m["names"], m["elem"], m["mw"], m["elements"], 8,
+                                 cfg["t_range"], cfg["p_range_atm"])
+        J = om.jacobian(p, y)
+        rad = [np.abs(np.linalg.eigvals(J[i])).max() for i in range(len(p))]
+        print("  spectral radius of J at 8 states: " + " ".join(f"{r:.2e}" for r in rad))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:] or None)
