@@ -1,0 +1,207 @@
+/* ck.h — batched constant-pressure chemical kinetics on one GPU (sm_103a).
+ *
+ * C ABI of the library built from paper_1608_05794_gb300/csrc.  It evaluates
+ * and integrates many independent homogeneous constant-pressure reactors —
+ * one per CFD cell after operator splitting — as described by Stone, Alferman
+ * & Niemeyer, "Accelerating finite-rate chemical kinetics with coprocessors"
+ * (arXiv 1608.05794):
+ *   Sec. 3  source terms: Eqs. ydot, tdot (state y = (T, Y_1..Y_S)), wdot,
+ *           kfor (Arrhenius), krev and kc (reverse rates through K_c from the
+ *           NASA-7 fits of Eq. tfits), third-body and Lindemann c_i;
+ *   Sec. 2  RKF45 (tableau of App. B) and ROS4 in transformed form
+ *           (coefficients of App. C), each driven by Algorithm 1;
+ *   Sec. 6  the analytic Jacobian that the paper recommends over finite
+ *           differences.
+ *
+ * Conventions for every call below.
+ *   - Units are SI: T in K, p in Pa, concentrations in mol/m^3, molar masses
+ *     in kg/mol, activation energies in J/mol, time in s.
+ *   - A reactor state is n = S + 1 doubles: y[0] = T, y[1+k] = Y_k (mass
+ *     fraction of species k).  Batches are row-major: reactor i occupies
+ *     y[i*n .. i*n+n-1].
+ *   - Array arguments may be device pointers (cudaMalloc, torch CUDA
+ *     tensors) or host pointers.  With device pointers the call only enqueues
+ *     work on `stream` (a cudaStream_t, NULL for the legacy default stream)
+ *     and returns; the caller keeps the buffers alive until the stream has
+ *     reached that point.  If any array argument of a call is host memory,
+ *     the library stages every array through device memory on `stream`,
+ *     waits for the stream, and returns with the host arrays updated.
+ *   - Arrays are owned by the caller; the library never frees them.  Objects
+ *     (ck_mech) are owned by the library and freed by their _free call.
+ *   - Every call returns CK_OK (0) or a positive call status (CK_E*);
+ *     ck_last_error() describes the most recent failure of this thread.
+ *     Per-reactor outcomes go to status[] (CK_R_*).  The library never traps
+ *     or aborts the process.
+ */
+#ifndef CK_H
+#define CK_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Call status. */
+enum {
+  CK_OK = 0,
+  CK_EINVAL = 1,   /* bad argument or mechanism */
+  CK_ECUDA = 2,    /* a CUDA call failed (see ck_last_error) */
+  CK_ENOMEM = 3,   /* device allocation failed */
+  CK_AGAIN = 4,    /* resource temporarily insufficient */
+  CK_TIMEOUT = 5,  /* a bounded device wait gave up */
+  CK_ERANGE = 6    /* size beyond a documented limit */
+};
+
+/* Per-reactor status of the integrators (status[i]).  A reactor that does
+ * not finish keeps its last accepted state. */
+enum {
+  CK_R_OK = 0,
+  CK_R_MAXSTEPS = 1,  /* opts.max_steps attempted steps without reaching dt */
+  CK_R_HMIN = 2,      /* step size fell below 1e-15 * dt */
+  CK_R_NONFINITE = 3, /* trial states stayed NaN/Inf until the step size collapsed */
+  CK_R_SINGULAR = 4,  /* ROS4: 10 consecutive singular iteration matrices */
+  CK_R_BADINPUT = 5   /* non-finite state, T <= 0, p <= 0 or dt < 0 */
+};
+
+/* Limits of this build. */
+#define CK_MAX_SPECIES 128
+#define CK_MAX_REACTIONS 32767
+
+typedef struct ck_mech ck_mech;
+
+/* Mechanism description (host arrays, copied by ck_load_mechanism).
+ * Reaction i has reactant slots reac[3i..3i+2] and product slots
+ * prod[3i..3i+2] holding species indices, padded with -1; a species listed
+ * twice has stoichiometric coefficient 2 (at most 3 slots per side, Eq. wdot).
+ * arrh[3i..3i+2] = (A, beta, Ea) of Eq. kfor with A in SI units for the
+ * reaction's order (one order higher for third-body reactions).  rtype: 0
+ * elementary (c_i = 1), 1 third-body (c_i = [M]), 2 Lindemann fall-off
+ * (c_i = P_r/(1+P_r), P_r = k0 [M]/k_inf with k0 from arrh0 and k_inf from
+ * arrh).  [M] = sum_k eff_ik [X_k] with eff_ik from the CSR arrays
+ * eff_ptr[R+1] / eff_sp / eff_val and 1 for unlisted species.  reversible:
+ * 1 = k_r from K_c (Eqs. krev, kc), 0 = irreversible.  nasa[S][2][7] holds
+ * the NASA-7 coefficients a1..a7 of the low (index 0, T < t_mid) and high
+ * ranges (Eq. tfits).  elem_count[S][n_elements] (optional, may be NULL)
+ * enables the atom-balance check; elem_mass[n_elements] (optional) enables
+ * the check of mw against the compositions. */
+typedef struct {
+  int32_t n_species, n_reactions;
+  const double* mw;
+  const double* nasa;
+  const double* t_mid;
+  const int32_t* reac;
+  const int32_t* prod;
+  const double* arrh;
+  const int32_t* rtype;
+  const int32_t* reversible;
+  const double* arrh0;
+  const int32_t* eff_ptr;
+  const int32_t* eff_sp;
+  const double* eff_val;
+  int32_t n_elements;
+  const int32_t* elem_count;
+  const double* elem_mass;
+} ck_mech_desc;
+
+/* Solver options.  The paper leaves the step-size controller unspecified
+ * (Sec. 5.2: both solvers share h0 estimation and h adaptation); this
+ * library's reading: weighted RMS error norm with weights atol + rtol
+ * max(|y|, |y*|); accept iff err < 1; h <- h min(5, max(0.2, 0.9 err^(-1/q)))
+ * with q = 4 (ROS4) or 5 (RKF45), no growth right after a rejection; h0 from
+ * the Hairer-Norsett-Wanner starting-step algorithm; last step clamped to
+ * end exactly at dt. */
+typedef struct {
+  double rtol;      /* relative tolerance (> 0) */
+  double atol;      /* absolute tolerance (> 0) */
+  double h0;        /* > 0: first step size; 0: estimate */
+  double fixed_h;   /* > 0: constant step, no error control (order tests) */
+  int32_t max_steps;/* attempted steps per reactor (accepted + rejected) */
+  int32_t precision;/* 0: FP64 throughout */
+  int32_t variant;  /* 0: default launch shape; > 0: warps per reactor team */
+  int32_t reserved;
+} ck_solver_opts;
+
+/* Fills *opts with rtol 1e-9, atol 1e-12, h0 0, fixed_h 0, max_steps 100000. */
+void ck_default_opts(ck_solver_opts* opts);
+
+/* Validate a mechanism, pack it into device tables on the current device
+ * and return a handle.  Packing (the paper's "binary database", Sec. 5):
+ * log2 A, Ea/(R ln 2) and beta per reaction; the Gibbs, enthalpy and heat
+ * capacity polynomials pre-divided for FP64-lean evaluation; a
+ * species -> reaction table for the team kernels.  Checks: sizes within
+ * CK_MAX_*, indices in range, A > 0, finite coefficients, mw > 0, and atom
+ * balance of every reaction when elem_count is given.  Returns CK_EINVAL
+ * with a message on failure (nothing allocated), CK_ENOMEM/CK_ECUDA on
+ * device failures. */
+int ck_load_mechanism(const ck_mech_desc* desc, ck_mech** out);
+/* Free a handle (device tables included).  NULL is allowed. */
+int ck_free_mechanism(ck_mech* mech);
+/* Sizes of a loaded mechanism. */
+int ck_mech_info(const ck_mech* mech, int32_t* n_species, int32_t* n_reactions);
+
+/* Right-hand side of Eqs. ydot/tdot for n reactors: dydt[i*(S+1)+0] = dT/dt,
+ * dydt[i*(S+1)+1+k] = dY_k/dt.  p[n] Pa, y[n][S+1].  One thread per reactor. */
+int ck_rhs(const ck_mech* mech, int64_t n, const double* p, const double* y, double* dydt,
+           void* stream);
+
+/* Analytic Jacobian jac[i][r][c] = d f_r / d y_c ([n][S+1][S+1], row-major per
+ * reactor) of the constant-pressure system at (p[i], y[i]).  One CTA per
+ * reactor. */
+int ck_jacobian(const ck_mech* mech, int64_t n, const double* p, const double* y, double* jac,
+                void* stream);
+
+/* Batched dense LU with partial pivoting (the linear algebra of the ROS4
+ * stages, Sec. 2).  a[batch][dim][dim] row-major, factored in place into the
+ * unit lower and upper triangles; piv[batch][dim] = row exchanged with row k;
+ * info[batch] = 0 or k+1 when pivot k is zero or not finite.  dim <= 128. */
+int ck_lu_factor(int64_t batch, int32_t dim, double* a, int32_t* piv, int32_t* info, void* stream);
+/* Solve A x = b in place for every matrix factored by ck_lu_factor. */
+int ck_lu_solve(int64_t batch, int32_t dim, const double* lu, const int32_t* piv, double* b,
+                void* stream);
+
+/* Integrate reactor i from t = 0 to dt[i] with ROS4 (Sec. 2, App. C:
+ * four-stage L-stable Rosenbrock, transformed form, analytic Jacobian,
+ * one LU per step, error = sum E_i u_i) under Algorithm 1.  y[n][S+1] is
+ * overwritten with the final states.  h_inout[n] (may be NULL): on entry a
+ * positive value is the first step size; on exit the step size proposed
+ * after the last accepted step.  steps[n][2] (may be NULL): accepted and
+ * rejected steps.  status[n]: CK_R_*.  opts may be NULL for the defaults.
+ * One CTA per reactor; reactors are handed out by a device work queue. */
+int ck_integrate_ros4(const ck_mech* mech, int64_t n, const double* p, double* y, const double* dt,
+                      double* h_inout, const ck_solver_opts* opts, int32_t* steps, int32_t* status,
+                      void* stream);
+/* Same with RKF45 (Sec. 2, App. B: six stages, fourth-order solution
+ * propagated, error = sum (bh - b) k).  One thread per reactor; each thread
+ * takes the next reactor from the work queue when its reactor finishes. */
+int ck_integrate_rkf45(const ck_mech* mech, int64_t n, const double* p, double* y, const double* dt,
+                       double* h_inout, const ck_solver_opts* opts, int32_t* steps, int32_t* status,
+                       void* stream);
+
+/* Algorithmic FP64 work, counted from the loaded tables, in FP64 pipe
+ * instructions (an FMA, a multiply, an add and a divide count one each; a
+ * 2^x counts 8, the cost of the table-driven evaluation this library uses):
+ * one RHS, the Jacobian beyond the RHS it also returns, one LU, one pair of
+ * triangular solves, one ROS4 step (Jacobian, 3 RHS, LU, 4 solves, vector
+ * work) and one RKF45 step (6 RHS, vector work); exps per RHS; and the
+ * algorithmic bytes per reactor (state in and out, p, dt, status). */
+typedef struct {
+  double rhs_fp64, rhs_exps, jac_fp64, lu_fp64, solve_fp64;
+  double ros4_step_fp64, rkf45_step_fp64;
+  double rhs_bytes, integrate_bytes;
+} ck_work_counts;
+int ck_count_work(const ck_mech* mech, ck_work_counts* out);
+
+/* Device error word of a mechanism (bit 1: a bounded shared-memory staging
+ * wait gave up).  Synchronizes the device; clears the word when reset != 0. */
+int ck_device_errors(const ck_mech* mech, int32_t* bits, int32_t reset);
+
+const char* ck_status_str(int code);
+const char* ck_last_error(void);
+const char* ck_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CK_H */

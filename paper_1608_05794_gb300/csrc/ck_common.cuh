@@ -1,0 +1,144 @@
+// Device-side data layout and arithmetic shared by the CUDA kernels of the
+// batched constant-pressure reactor library (Stone, Alferman & Niemeyer,
+// arXiv 1608.05794, Sec. 3 source terms; Sec. 2 integrators).
+//
+// FP64 is the scarce resource on this GPU (about 1.2 TFLOP/s against
+// 70 TFLOP/s FP32), so the tables are pre-scaled at load time to save FP64
+// instructions at run time: rate constants are kept as base-2 logarithms
+// and evaluated with a table-driven 2^x (8 FP64 instructions), and the
+// Gibbs polynomials are pre-divided by ln 2.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace ck {
+
+constexpr double R_GAS = 8.314462618;       // J/(mol K)
+constexpr double P_STD = 101325.0;          // p0 of Eq. kc, Pa
+constexpr double LN2 = 0.6931471805599453094;
+constexpr double INV_LN2 = 1.4426950408889634074;
+constexpr double LOG2_P0_OVER_R = 13.573007627848395117;  // log2(101325 / 8.314462618)
+
+// One reaction, 80 bytes, read uniformly by all lanes (thread-per-reactor
+// kernels) or by one lane per reaction (team kernels).
+struct __align__(16) RxnRec {
+  double lA2;    // log2 A (SI)
+  double beta;   // temperature exponent
+  double EoR2;   // Ea / (R ln 2), K
+  double lA02;   // Lindemann low-pressure limit: log2 A0
+  double beta0;
+  double E0oR2;
+  int16_t sp[6];    // reactant slots 0..2, product slots 3..5, -1 padded
+  int8_t type;      // 0 elementary, 1 third-body, 2 Lindemann
+  int8_t rev;       // 1 reversible through K_c
+  int8_t dnu;       // sum of product minus reactant coefficients
+  int8_t nreac, nprod, pad0;
+  int16_t eff_beg, eff_cnt;  // slice of the efficiency table (eff - 1 != 0)
+  int16_t pad1, pad2;
+};
+static_assert(sizeof(RxnRec) == 80, "RxnRec layout");
+
+// Per species and temperature range: 18 doubles
+//   cp/R  : c0 + c1 T + c2 T^2 + c3 T^3 + c4 T^4               [0..4]
+//   H/RT  : h0 + h1 T + h2 T^2 + h3 T^3 + h4 T^4 + h5 / T       [5..10]
+//   g/ln2 : (S/R - H/RT)/ln 2 = G0 ln T + G1 + G2 T + G3 T^2 + G4 T^3 + G5 T^4 + G6 / T   [11..17]
+constexpr int TH_STRIDE = 18;
+constexpr int TH_PER_SPECIES = 2 * TH_STRIDE;
+
+// Device view of a loaded mechanism.  All pointers are device memory (one
+// allocation, 16-byte aligned sections).
+struct DevMech {
+  int S, R, n;            // species, reactions, n = S + 1
+  int n_eff;              // entries of the efficiency table
+  int csr_nnz;            // entries of the species -> reaction table
+  int all_same_tmid;      // every species shares one T_mid
+  double tmid0;
+  const RxnRec* rxn;      // [R]
+  const double* thermo;   // [S][2][TH_STRIDE]
+  const double* tmid;     // [S]
+  const double* W;        // [S] kg/mol
+  const double* invW;     // [S]
+  const int16_t* eff_sp;  // [n_eff]
+  const double* eff_m1;   // [n_eff] efficiency - 1
+  const int32_t* csr_ptr; // [S+1] species -> (reaction, net nu) lists
+  const int32_t* csr_rx;  // [csr_nnz] reaction index << 8 | (nu + 8)
+  const double* tab;      // [256] 2^(j/256)
+};
+
+// ---------------------------------------------------------------- 2^x
+// Table-driven 2^x after Tang, "Table-driven implementation of the
+// exponential function in IEEE floating-point arithmetic" (ACM TOMS 15,
+// 1989), in base 2: x = e + j/256 + r with |r| <= 1/512, 2^x = 2^e T_j 2^r,
+// T_j = 2^(j/256) from a 256-entry table, 2^r - 1 by its degree-4 Taylor
+// polynomial in r ln 2 (truncation < 4e-17 relative).  The reduction is
+// exact (x - round_{1/256}(x) is representable), so the result is within
+// about one ulp.  |x| > 1000 falls back to the library exp2.
+struct Exp2Table {
+  double t[256];
+};
+
+__device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ tab) {
+  if (!(fabs(x) <= 1000.0)) return exp2(x);
+  const double SHIFT = 26388279066624.0;  // 1.5 * 2^44: ulp 2^-8
+  double t = x + SHIFT;
+  double kx = t - SHIFT;
+  double r = x - kx;
+  int i = (int)__double2loint(t);        // round(x * 256), low bits of t
+  int j = i & 255;
+  int e = i >> 8;                        // floor division by 256
+  const double c1 = 0.69314718055994530942;
+  const double c2 = 0.24022650695910071233;   // ln2^2/2
+  const double c3 = 0.055504108664821579953;  // ln2^3/6
+  const double c4 = 0.0096181291076284771620; // ln2^4/24
+  double q = fma(fma(fma(c4, r, c3), r, c2), r, c1) * r;
+  double tj = tab[j];
+  double res = fma(tj, q, tj);
+  long long b = __double_as_longlong(res) + ((long long)e << 52);
+  return __longlong_as_double(b);
+}
+
+// ---------------------------------------------------------------- statuses
+enum : int32_t { ST_OK = 0, ST_MAXSTEPS = 1, ST_HMIN = 2, ST_NONFINITE = 3, ST_SINGULAR = 4,
+                 ST_BADINPUT = 5 };
+
+// Step-control constants (the paper leaves the controller unspecified; these
+// are the readings shared with the CPU oracle's documentation).
+constexpr double FAC_MAX = 5.0, FAC_MIN = 0.2, SAFETY = 0.9;
+constexpr int SINGULAR_LIMIT = 10;
+
+// ROS4 coefficients, App. C Table ros4 (gamma is the table value 0.57282;
+// the table's b_i are the transformed-scheme weights m_i; a4j = a3j, a43 = 0
+// so the fourth stage reuses the third stage's f).
+constexpr double ROS_GAMMA = 0.57282;
+constexpr double ROS_A21 = 2.0;
+constexpr double ROS_A31 = 1.867943637803922, ROS_A32 = 0.2344449711399156;
+constexpr double ROS_C21 = -7.137615036412310;
+constexpr double ROS_C31 = 2.580708087951457, ROS_C32 = 0.6515950076447975;
+constexpr double ROS_C41 = -2.137148994382534, ROS_C42 = -0.3214669691237626,
+                 ROS_C43 = -0.6949742501781779;
+constexpr double ROS_M1 = 2.255570073418735, ROS_M2 = 0.2870493262186792,
+                 ROS_M3 = 0.4353179431840180, ROS_M4 = 1.093502252409163;
+constexpr double ROS_E1 = -0.2815431932141155, ROS_E2 = -0.07276199124938920,
+                 ROS_E3 = -0.1082196201495311, ROS_E4 = -1.093502252409163;
+
+// RKF45 tableau, App. B Table rkf45 (b: fourth-order weights, propagated;
+// bh: fifth-order weights; the error is sum (bh - b) k).
+constexpr double RK_A21 = 1.0 / 4.0;
+constexpr double RK_A31 = 3.0 / 32.0, RK_A32 = 9.0 / 32.0;
+constexpr double RK_A41 = 1932.0 / 2197.0, RK_A42 = -7200.0 / 2197.0, RK_A43 = 7296.0 / 2197.0;
+constexpr double RK_A51 = 439.0 / 216.0, RK_A52 = -8.0, RK_A53 = 3680.0 / 513.0,
+                 RK_A54 = -845.0 / 4104.0;
+constexpr double RK_A61 = -8.0 / 27.0, RK_A62 = 2.0, RK_A63 = -3544.0 / 2565.0,
+                 RK_A64 = 1859.0 / 4104.0, RK_A65 = -11.0 / 40.0;
+constexpr double RK_B1 = 25.0 / 216.0, RK_B3 = 1408.0 / 2565.0, RK_B4 = 2197.0 / 4104.0,
+                 RK_B5 = -1.0 / 5.0;
+constexpr double RK_D1 = 16.0 / 135.0 - 25.0 / 216.0, RK_D3 = 6656.0 / 12825.0 - 1408.0 / 2565.0,
+                 RK_D4 = 28561.0 / 56430.0 - 2197.0 / 4104.0, RK_D5 = -9.0 / 50.0 + 1.0 / 5.0,
+                 RK_D6 = 2.0 / 55.0;
+
+struct SolverParams {
+  double rtol, atol, h0, fixed_h;
+  int max_steps;
+};
+
+}  // namespace ck

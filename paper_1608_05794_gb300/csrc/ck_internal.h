@@ -1,0 +1,57 @@
+// Host-side internal interface between the C ABI (ck_api.cu) and the kernel
+// translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "ck_common.cuh"
+
+namespace ck {
+
+// Byte offsets of the sections of the staged table block (all 16-byte
+// aligned).  The block is [rxn | thermo | tmid | W | invW | eff_sp | eff_m1 | exp2].
+struct StageLayout {
+  uint32_t rx, th, tmid, W, invW, eff_sp, eff_m1, tab, bytes;
+};
+
+struct HostMech {
+  int device = -1;
+  DevMech d{};
+  StageLayout L{};
+  void* blob = nullptr;     // device allocation holding every table
+  size_t blob_bytes = 0;
+  int32_t* dev_err = nullptr;  // device error word (bounded waits that gave up)
+  // host copies used for work counting
+  std::vector<RxnRec> rx;
+  int S = 0, R = 0;
+};
+
+// Device-side error bits reported through HostMech::dev_err.
+enum : int32_t { DEVERR_STAGE_TIMEOUT = 1 };
+
+// Launch configuration knobs chosen by the host (variant / autotuner).
+struct LaunchCfg {
+  int team_warps = 0;   // warps per reactor for team kernels (0: heuristic)
+  int ctas_per_sm = 0;  // 0: as many as fit
+};
+
+cudaError_t launch_rhs(const HostMech& hm, int64_t n, const double* p, const double* y, double* f,
+                       cudaStream_t st);
+cudaError_t launch_jacobian(const HostMech& hm, int64_t n, const double* p, const double* y,
+                            double* jac, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t launch_lu_factor(int64_t batch, int dim, double* a, int32_t* piv, int32_t* info,
+                             cudaStream_t st);
+cudaError_t launch_lu_solve(int64_t batch, int dim, const double* lu, const int32_t* piv,
+                            double* b, cudaStream_t st);
+cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
+                        double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
+                        int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t launch_rkf45(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
+                         double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
+                         int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);
+
+int sm_count();
+
+}  // namespace ck

@@ -1,0 +1,372 @@
+// Team-per-reactor kernels: analytic Jacobian, batched dense LU / solve and
+// the ROS4 Rosenbrock integrator (Sec. 2 transformed form, App. C, driven by
+// Algorithm 1).  One CTA owns one reactor at a time and keeps its iteration
+// matrix I/(h gamma) - J in shared memory; CTAs pull reactors from a global
+// atomic counter (dynamic scheduling, granularity one reactor).
+#include <cuda_runtime.h>
+
+#include "ck_internal.h"
+#include "ck_team.cuh"
+
+namespace ck {
+
+__host__ __device__ __forceinline__ int team_bufs_doubles(int S, int R) { return 10 * S + 6 * R + 64; }
+
+__device__ __forceinline__ TeamBufs carve_bufs(double* base, int S, int R) {
+  TeamBufs b;
+  b.X = base;
+  b.g2 = b.X + S;
+  b.hRT = b.g2 + S;
+  b.cpR = b.hRT + S;
+  b.dcpR = b.cpR + S;
+  b.wd = b.dcpR + S;
+  b.aT = b.wd + S;
+  b.E = b.aT + S;
+  b.u = b.E + S;
+  b.cs = b.u + S;
+  b.q = b.cs + S;
+  b.ckf = b.q + R;
+  b.ckr = b.ckf + R;
+  b.w = b.ckr + R;
+  b.dqT = b.w + R;
+  b.D = b.dqT + R;
+  b.red = b.D + R;
+  return b;
+}
+
+// Next reactor index for this CTA from the global queue (same in every thread).
+__device__ __forceinline__ int team_next(int32_t* queue, int* slot) {
+  if (threadIdx.x == 0) *slot = atomicAdd(queue, 1);
+  __syncthreads();
+  const int r = *slot;
+  __syncthreads();
+  return r;
+}
+
+// ------------------------------------------------------------------ Jacobian
+__global__ void k_jacobian(DevMech d, int64_t N, const double* __restrict__ p,
+                           const double* __restrict__ y, double* __restrict__ jac) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = d.n;
+  double* J = sm;
+  double* ys = J + (size_t)n * n;
+  double* fs = ys + n;
+  TeamBufs b = carve_bufs(fs + n, d.S, d.R);
+  Mix x;
+  for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = y[r * n + i];
+    __syncthreads();
+    team_jacobian(d, d.tab, p[r], ys, fs, J, b, x);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) jac[r * (int64_t)n * n + e] = J[e];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ batched LU
+__global__ void k_lu_factor(int64_t batch, int dim, double* __restrict__ a, int32_t* __restrict__ piv,
+                            int32_t* __restrict__ info) {
+  extern __shared__ __align__(16) double sm[];
+  double* A = sm;
+  double* invd = A + (size_t)dim * dim;
+  int* pv = reinterpret_cast<int*>(invd + dim);
+  double* red = invd + 2 * dim;
+  const int64_t nn = (int64_t)dim * dim;
+  for (int64_t m = blockIdx.x; m < batch; m += gridDim.x) {
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) A[e] = a[m * nn + e];
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) pv[i] = i;
+    __syncthreads();
+    const int inf = team_lu(A, dim, pv, invd, red);
+    __syncthreads();
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) a[m * nn + e] = A[e];
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) piv[m * dim + i] = pv[i];
+    if (threadIdx.x == 0) info[m] = inf;
+    __syncthreads();
+  }
+}
+
+__global__ void k_lu_solve(int64_t batch, int dim, const double* __restrict__ lu,
+                           const int32_t* __restrict__ piv, double* __restrict__ bvec) {
+  extern __shared__ __align__(16) double sm[];
+  double* A = sm;
+  double* invd = A + (size_t)dim * dim;
+  int* pv = reinterpret_cast<int*>(invd + dim);
+  double* x = invd + 2 * dim;
+  const int64_t nn = (int64_t)dim * dim;
+  for (int64_t m = blockIdx.x; m < batch; m += gridDim.x) {
+    for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) A[e] = lu[m * nn + e];
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) {
+      pv[i] = piv[m * dim + i];
+      x[i] = bvec[m * dim + i];
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) invd[i] = 1.0 / A[(size_t)i * dim + i];
+    __syncthreads();
+    team_lu_solve(A, dim, pv, invd, x);
+    for (int i = threadIdx.x; i < dim; i += blockDim.x) bvec[m * dim + i] = x[i];
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ ROS4
+// Weighted RMS norm over the team (reading shared with the oracle:
+// sqrt(mean (e_i / (atol + rtol max(|y_i|, |ynew_i|)))^2)).
+__device__ __forceinline__ double team_wrms(int n, const double* e, const double* y0,
+                                            const double* y1, double rtol, double atol, double* red) {
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double sc = atol + rtol * fmax(fabs(y0[i]), fabs(y1[i]));
+    const double v = e[i] / sc;
+    s = fma(v, v, s);
+  }
+  s = team_sum(s, red);
+  return sqrt(s / n);
+}
+
+// Initial step, Hairer-Norsett-Wanner starting-step algorithm (order 4).
+__device__ double team_h0(const DevMech& d, double p, const double* y0, double tspan, double rtol,
+                          double atol, double* f0, double* y1, double* f1, TeamBufs& b, Mix& x) {
+  const int n = d.n;
+  team_rhs(d, d.tab, p, y0, f0, b, x);
+  double s0 = 0.0, s1 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double sc = atol + rtol * fabs(y0[i]);
+    s0 = fma(y0[i] / sc, y0[i] / sc, s0);
+    s1 = fma(f0[i] / sc, f0[i] / sc, s1);
+  }
+  const double d0 = sqrt(team_sum(s0, b.red) / n);
+  const double d1 = sqrt(team_sum(s1, b.red) / n);
+  const double ha = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y1[i] = fma(ha, f0[i], y0[i]);
+  team_sync();
+  team_rhs(d, d.tab, p, y1, f1, b, x);
+  double s2 = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double sc = atol + rtol * fabs(y0[i]);
+    const double v = (f1[i] - f0[i]) / sc;
+    s2 = fma(v, v, s2);
+  }
+  const double d2 = sqrt(team_sum(s2, b.red) / n) / ha;
+  const double dm = fmax(d1, d2);
+  const double hb = (dm <= 1e-15) ? fmax(1e-6, ha * 1e-3) : pow(0.01 / dm, 0.2);
+  return fmin(fmin(100.0 * ha, hb), tspan);
+}
+
+__global__ void k_ros4(DevMech d, int64_t N, const double* __restrict__ p, double* __restrict__ y,
+                       const double* __restrict__ dt, double* h_io, SolverParams sp, int32_t* steps,
+                       int32_t* status, int32_t* queue) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int slot;
+  const int n = d.n;
+  double* M = sm;
+  double* yv = M + (size_t)n * n;
+  double* F0 = yv + n;
+  double* F = F0 + n;
+  double* Yt = F + n;
+  double* u1 = Yt + n;
+  double* u2 = u1 + n;
+  double* u3 = u2 + n;
+  double* u4 = u3 + n;
+  double* invd = u4 + n;
+  int* piv = reinterpret_cast<int*>(invd + n);
+  TeamBufs b = carve_bufs(invd + 2 * n, d.S, d.R);
+  Mix x;
+  const bool fixed = sp.fixed_h > 0.0;
+  const int tid = threadIdx.x, P = blockDim.x;
+  for (;;) {
+    const int r = team_next(queue, &slot);
+    if (r >= N) break;
+    for (int i = tid; i < n; i += P) yv[i] = y[(int64_t)r * n + i];
+    const double pr = p[r];
+    const double tf = dt[r];
+    __syncthreads();
+    int bad = 0;
+    for (int i = tid; i < n; i += P) bad |= !isfinite(yv[i]);
+    bad = __syncthreads_or(bad);
+    bad |= !(pr > 0.0) || !isfinite(pr) || !(yv[0] > 0.0) || !isfinite(tf) || !(tf >= 0.0);
+    int st = ST_OK, acc = 0, rej = 0;
+    double h = 0.0;
+    if (bad) {
+      st = ST_BADINPUT;
+    } else if (tf > 0.0) {
+      if (fixed) h = sp.fixed_h;
+      else if (h_io && h_io[r] > 0.0) h = h_io[r];
+      else if (sp.h0 > 0.0) h = sp.h0;
+      else h = team_h0(d, pr, yv, tf, sp.rtol, sp.atol, F0, Yt, F, b, x);
+      const double hmin = 1e-15 * tf;
+      double t = 0.0;
+      bool last_rej = false, last_nf = false;
+      int sing_run = 0;
+      while (t < tf) {
+        if (acc + rej >= sp.max_steps) { st = ST_MAXSTEPS; break; }
+        const bool clamped = h >= tf - t;
+        const double hh = clamped ? tf - t : h;
+        if (hh < hmin) { st = last_nf ? ST_NONFINITE : ST_HMIN; break; }
+        // J and f at y; M = I/(hh gamma) - J; LU
+        team_jacobian(d, d.tab, pr, yv, F0, M, b, x);
+        const double dg = 1.0 / (hh * ROS_GAMMA);
+        for (int e = tid; e < n * n; e += P) M[e] = -M[e];
+        team_sync();
+        for (int i = tid; i < n; i += P) M[(size_t)i * n + i] += dg;
+        team_sync();
+        const int info = team_lu(M, n, piv, invd, b.red);
+        if (info) {
+          ++rej;
+          if (++sing_run >= SINGULAR_LIMIT) { st = ST_SINGULAR; break; }
+          h = 0.5 * hh;
+          last_rej = true;
+          continue;
+        }
+        sing_run = 0;
+        const double ih = 1.0 / hh;
+        // stage 1: M u1 = f(y)
+        for (int i = tid; i < n; i += P) u1[i] = F0[i];
+        team_sync();
+        team_lu_solve(M, n, piv, invd, u1);
+        // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
+        for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A21, u1[i], yv[i]);
+        team_sync();
+        team_rhs(d, d.tab, pr, Yt, F, b, x);
+        for (int i = tid; i < n; i += P) u2[i] = fma(ROS_C21 * ih, u1[i], F[i]);
+        team_sync();
+        team_lu_solve(M, n, piv, invd, u2);
+        // stage 3: M u3 = f(y + a31 u1 + a32 u2) + (c31 u1 + c32 u2)/h
+        for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A32, u2[i], fma(ROS_A31, u1[i], yv[i]));
+        team_sync();
+        team_rhs(d, d.tab, pr, Yt, F, b, x);
+        for (int i = tid; i < n; i += P)
+          u3[i] = fma(ROS_C32 * ih, u2[i], fma(ROS_C31 * ih, u1[i], F[i]));
+        team_sync();
+        team_lu_solve(M, n, piv, invd, u3);
+        // stage 4: same argument as stage 3 (a4j = a3j, a43 = 0), so f is reused
+        for (int i = tid; i < n; i += P)
+          u4[i] = fma(ROS_C43 * ih, u3[i], fma(ROS_C42 * ih, u2[i], fma(ROS_C41 * ih, u1[i], F[i])));
+        team_sync();
+        team_lu_solve(M, n, piv, invd, u4);
+        // y* = y + sum m_i u_i (into Yt), e = sum E_i u_i (into F)
+        int nf = 0;
+        for (int i = tid; i < n; i += P) {
+          const double yn =
+              fma(ROS_M4, u4[i], fma(ROS_M3, u3[i], fma(ROS_M2, u2[i], fma(ROS_M1, u1[i], yv[i]))));
+          Yt[i] = yn;
+          F[i] = fma(ROS_E4, u4[i], fma(ROS_E3, u3[i], fma(ROS_E2, u2[i], ROS_E1 * u1[i])));
+          nf |= !isfinite(yn);
+        }
+        nf = __syncthreads_or(nf);
+        if (fixed) {
+          for (int i = tid; i < n; i += P) yv[i] = Yt[i];
+          team_sync();
+          t = clamped ? tf : t + hh;
+          ++acc;
+          continue;
+        }
+        const double e = team_wrms(n, F, yv, Yt, sp.rtol, sp.atol, b.red);
+        if (nf || !isfinite(e)) {
+          ++rej;
+          h = FAC_MIN * hh;
+          last_rej = true;
+          last_nf = true;
+          continue;
+        }
+        last_nf = false;
+        if (e < 1.0) {
+          for (int i = tid; i < n; i += P) yv[i] = Yt[i];
+          team_sync();
+          t = clamped ? tf : t + hh;
+          ++acc;
+          double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(e, -0.25)));
+          if (last_rej) fac = fmin(1.0, fac);
+          h = hh * fac;
+          last_rej = false;
+        } else {
+          ++rej;
+          h = hh * fmax(FAC_MIN, SAFETY * pow(e, -0.25));
+          last_rej = true;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += P) y[(int64_t)r * n + i] = yv[i];
+    if (tid == 0) {
+      if (h_io && st != ST_BADINPUT && tf > 0.0) h_io[r] = h;
+      if (steps) {
+        steps[2 * (int64_t)r] = acc;
+        steps[2 * (int64_t)r + 1] = rej;
+      }
+      status[r] = st;
+    }
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------ launchers
+static int team_threads(int n, const LaunchCfg& cfg) {
+  int w = cfg.team_warps;
+  if (w <= 0) w = (n <= 24) ? 1 : (n <= 64 ? 2 : 4);
+  if (w > 8) w = 8;
+  return 32 * w;
+}
+
+template <class K>
+static int team_grid(K kernel, int threads, size_t smem, int64_t work, const LaunchCfg& cfg) {
+  if (smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, smem);
+  if (per_sm < 1) per_sm = 1;
+  if (cfg.ctas_per_sm > 0 && cfg.ctas_per_sm < per_sm) per_sm = cfg.ctas_per_sm;
+  int64_t g = (int64_t)per_sm * sm_count();
+  if (work < g) g = work;
+  return (int)(g < 1 ? 1 : g);
+}
+
+size_t ros4_smem_bytes(int n, int S, int R) {
+  return sizeof(double) * ((size_t)n * n + 11 * (size_t)n + team_bufs_doubles(S, R));
+}
+
+cudaError_t launch_jacobian(const HostMech& hm, int64_t n, const double* p, const double* y,
+                            double* jac, cudaStream_t st, const LaunchCfg& cfg) {
+  if (n <= 0) return cudaSuccess;
+  const int nn = hm.d.n;
+  const size_t smem = sizeof(double) * ((size_t)nn * nn + 2 * nn + team_bufs_doubles(hm.S, hm.R));
+  const int threads = team_threads(nn, cfg);
+  const int grid = team_grid(k_jacobian, threads, smem, n, cfg);
+  k_jacobian<<<grid, threads, smem, st>>>(hm.d, n, p, y, jac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_factor(int64_t batch, int dim, double* a, int32_t* piv, int32_t* info,
+                             cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * ((size_t)dim * dim + 2 * dim + 64);
+  LaunchCfg cfg;
+  const int threads = team_threads(dim, cfg);
+  const int grid = team_grid(k_lu_factor, threads, smem, batch, cfg);
+  k_lu_factor<<<grid, threads, smem, st>>>(batch, dim, a, piv, info);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lu_solve(int64_t batch, int dim, const double* lu, const int32_t* piv,
+                            double* b, cudaStream_t st) {
+  if (batch <= 0) return cudaSuccess;
+  const size_t smem = sizeof(double) * ((size_t)dim * dim + 3 * dim);
+  LaunchCfg cfg;
+  const int threads = team_threads(dim, cfg);
+  const int grid = team_grid(k_lu_solve, threads, smem, batch, cfg);
+  k_lu_solve<<<grid, threads, smem, st>>>(batch, dim, lu, piv, b);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
+                        double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
+                        int32_t* queue, cudaStream_t st, const LaunchCfg& cfg) {
+  if (n <= 0) return cudaSuccess;
+  const int nn = hm.d.n;
+  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.R);
+  const int threads = team_threads(nn, cfg);
+  const int grid = team_grid(k_ros4, threads, smem, n, cfg);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  k_ros4<<<grid, threads, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
+  return cudaGetLastError();
+}
+
+}  // namespace ck

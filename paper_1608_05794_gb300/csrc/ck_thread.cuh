@@ -1,0 +1,113 @@
+// Thread-per-reactor right-hand side ("shallow" vectorisation, Sec. 4 of
+// the paper: one ODE system per SIMT lane).  Every lane walks the same
+// reaction list, so table reads are uniform (broadcast) and the only
+// divergence is the per-species choice of NASA-7 range (Sec. 4, "Select").
+#pragma once
+#include "ck_common.cuh"
+
+namespace ck {
+
+// Tables as seen by one kernel: shared memory when staged, else global.
+struct MechView {
+  int S, R;
+  const RxnRec* rx;
+  const double* th;
+  const double* tmid;
+  const double* W;
+  const double* invW;
+  const int16_t* eff_sp;
+  const double* eff_m1;
+  const double* tab;  // 2^(j/256), j = 0..255
+};
+
+// f = (dT/dt, dY_k/dt) at state y (Eqs. ydot, tdot, wdot, kfor, krev, kc,
+// tfits).  y and f are strided (element k at y[k*ys]); X, g2, wd are per-lane
+// scratch of S doubles.
+//   rho = p Wbar / (R T), [X_k] = rho Y_k / W_k,
+//   k_f = 2^(log2 A + beta log2 T - Ea/(R T ln 2)),
+//   log2 K_c = sum_j nu_j g_j / ln 2 + dnu log2(p0/(R T)), k_r = 2^(log2 k_f - log2 K_c),
+//   c = 1, [M], or P_r/(1+P_r) with P_r = 2^(log2 k0 - log2 k_inf) [M],
+//   q = c (k_f prod [X]^nu' - k_r prod [X]^nu''),  wdot_k = sum (nu'' - nu') q,
+//   dY_k/dt = wdot_k W_k / rho, dT/dt = -T sum_k (H_k/RT) wdot_k / (rho sum_k Y_k (cp_k/R)/W_k).
+__device__ __forceinline__ void rhs_thread(const MechView& m, double p, const double* y, int ys,
+                                           double* f, int fs, double* X, double* g2, double* wd) {
+  const int S = m.S;
+  const double T = y[0];
+  const double invT = 1.0 / T;
+  const double lnT = log(T);
+  const double log2T = lnT * INV_LN2;
+  const double T2 = T * T, T3 = T2 * T, T4 = T3 * T;
+  double sumYW = 0.0;
+  for (int k = 0; k < S; ++k) sumYW = fma(y[(1 + k) * ys], m.invW[k], sumYW);
+  const double rho = p / (R_GAS * T * sumYW);
+  double Ctot = 0.0;
+  for (int k = 0; k < S; ++k) {
+    const double xk = rho * (y[(1 + k) * ys] * m.invW[k]);
+    X[k] = xk;
+    Ctot += xk;
+    const double* a = m.th + k * TH_PER_SPECIES + (T < m.tmid[k] ? 0 : TH_STRIDE);
+    double g = fma(a[11], lnT, a[12]);
+    g = fma(a[13], T, g);
+    g = fma(a[14], T2, g);
+    g = fma(a[15], T3, g);
+    g = fma(a[16], T4, g);
+    g2[k] = fma(a[17], invT, g);
+    wd[k] = 0.0;
+  }
+  const double lp2 = LOG2_P0_OVER_R - log2T;  // log2(p0 / (R T))
+  for (int i = 0; i < m.R; ++i) {
+    const RxnRec& r = m.rx[i];
+    const double l2kf = fma(-r.EoR2, invT, fma(r.beta, log2T, r.lA2));
+    const double kf = ck_exp2(l2kf, m.tab);
+    double fwd = X[r.sp[0]];
+    if (r.nreac > 1) fwd *= X[r.sp[1]];
+    if (r.nreac > 2) fwd *= X[r.sp[2]];
+    double net = kf * fwd;
+    if (r.rev) {
+      double l2kc = (double)r.dnu * lp2;
+      l2kc += g2[r.sp[3]];
+      if (r.nprod > 1) l2kc += g2[r.sp[4]];
+      if (r.nprod > 2) l2kc += g2[r.sp[5]];
+      l2kc -= g2[r.sp[0]];
+      if (r.nreac > 1) l2kc -= g2[r.sp[1]];
+      if (r.nreac > 2) l2kc -= g2[r.sp[2]];
+      const double kr = ck_exp2(l2kf - l2kc, m.tab);
+      double rv = X[r.sp[3]];
+      if (r.nprod > 1) rv *= X[r.sp[4]];
+      if (r.nprod > 2) rv *= X[r.sp[5]];
+      net = fma(-kr, rv, net);
+    }
+    double q = net;
+    if (r.type) {
+      double M = Ctot;
+      for (int e = r.eff_beg; e < r.eff_beg + r.eff_cnt; ++e) M = fma(m.eff_m1[e], X[m.eff_sp[e]], M);
+      if (r.type == 1) {
+        q = M * net;
+      } else {
+        const double l2k0 = fma(-r.E0oR2, invT, fma(r.beta0, log2T, r.lA02));
+        const double Pr = ck_exp2(l2k0 - l2kf, m.tab) * M;
+        q = net * (Pr / (1.0 + Pr));
+      }
+    }
+    wd[r.sp[0]] -= q;
+    if (r.nreac > 1) wd[r.sp[1]] -= q;
+    if (r.nreac > 2) wd[r.sp[2]] -= q;
+    wd[r.sp[3]] += q;
+    if (r.nprod > 1) wd[r.sp[4]] += q;
+    if (r.nprod > 2) wd[r.sp[5]] += q;
+  }
+  const double invrho = 1.0 / rho;
+  double cpm = 0.0, hw = 0.0;
+  for (int k = 0; k < S; ++k) {
+    const double* a = m.th + k * TH_PER_SPECIES + (T < m.tmid[k] ? 0 : TH_STRIDE);
+    double cp = fma(a[4], T4, fma(a[3], T3, fma(a[2], T2, fma(a[1], T, a[0]))));
+    double h = fma(a[10], invT, fma(a[9], T4, fma(a[8], T3, fma(a[7], T2, fma(a[6], T, a[5])))));
+    const double w = wd[k];
+    cpm = fma(y[(1 + k) * ys] * m.invW[k], cp, cpm);
+    hw = fma(h, w, hw);
+    f[(1 + k) * fs] = w * (m.W[k] * invrho);
+  }
+  f[0] = -T * hw / (rho * cpm);
+}
+
+}  // namespace ck
