@@ -1,0 +1,390 @@
+"""Benchmark of the batched reactor path on GB300.
+
+One step = one pass of the whole hot path over the batch of the medium
+workload (53 species / 325 reactions, 131072 constant-pressure reactors):
+one right-hand-side evaluation of every reactor, ROS4 integration of every
+reactor over dt = 1e-5 s and RKF45 integration of every reactor over the same
+dt (rtol 1e-9, atol 1e-12).  ``value`` is reactor integrations per second
+(2 per reactor per step) with inputs resident in HBM; the RHS throughput
+benchmark (1000 repeats of the RHS over the batch) is reported beside it.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): each rank integrates its own batch (weak scaling, no
+collective on the data path); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reactor integrations/sec and RHS evals/sec @1 GB300 vs roofline; serving p50/p99 ms"
+UNIT = "reactor-integrations/s"
+WORKLOAD = "medium"
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 (2 flops per DFMA) at the maximum SM clock
+L2_BYTES = 129 * 2 ** 20
+
+
+def _rank_env():
+    return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), int(
+        os.environ.get("LOCAL_RANK", "0"))
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _traffic_for(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it matches the
+    current kernel sources."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        info = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    ent = info.get(kernel)
+    if not ent:
+        return None
+    from paper_1608_05794_gb300.build import sources_digest
+    if ent.get("sources_digest") != sources_digest():
+        return None
+    return ent.get("bytes_per_launch")
+
+
+def cpu_baseline(sample: int, threads: int = 0):
+    """The oracle (as it stands) on the host cores over a bounded sample of
+    the same workload: ROS4 + RKF45 of `sample` reactors and one RHS each."""
+    from oracle import ORA_RKF45, ORA_ROS4, Oracle, OracleMech
+    from synth.configs import CONFIGS, load_mechanism, reactor_states
+    cfg = CONFIGS[WORKLOAD]
+    om = OracleMech(load_mechanism(cfg["mech"]))
+    y, p = reactor_states(WORKLOAD, n=sample)
+    cores = threads if threads > 0 else Oracle().hardware_threads()
+    t0 = time.perf_counter()
+    om.rhs(p, y)
+    om.integrate(ORA_ROS4, p, y, cfg["dt"], nthreads=cores)
+    om.integrate(ORA_RKF45, p, y, cfg["dt"], nthreads=cores)
+    el = time.perf_counter() - t0
+    return {"value": 2 * sample / el, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {sample} of the {cfg['n_reactors']} medium-workload reactors: one RHS, "
+                      f"ROS4 and RKF45 over dt={cfg['dt']:g} s each, C++ oracle threaded over reactors",
+            "seconds": el}
+
+
+def run_reference(args):
+    rank, world, _ = _rank_env()
+    if rank != 0:
+        return
+    sample = args.cpu_sample
+    vals, secs = [], []
+    for i in range(args.warmup + args.steps):
+        r = cpu_baseline(sample)
+        if i >= args.warmup:
+            vals.append(r["value"])
+            secs.append(r["seconds"])
+    v = float(np.mean(vals))
+    from synth.configs import CONFIGS
+    cfg = CONFIGS[WORKLOAD]
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * float(np.mean(secs)),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": _config_dict(cfg),
+            "cpu_baseline": {"kind": "oracle", "cores": r["cores"], "sample": r["sample"], "value": v,
+                             "unit": UNIT},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config_dict(cfg):
+    return {"workload": f"{WORKLOAD}: {cfg['n_species']} species / {cfg['n_reactions']} reactions "
+                        f"({cfg['n_thirdbody']} third-body, {cfg['n_falloff']} Lindemann), "
+                        f"{cfg['n_reactors']} constant-pressure reactors, RHS + ROS4 + RKF45 over "
+                        f"dt={cfg['dt']:g} s, rtol 1e-9, atol 1e-12",
+            "reactors": cfg["n_reactors"], "species": cfg["n_species"], "reactions": cfg["n_reactions"],
+            "dt": cfg["dt"], "rtol": 1e-9, "atol": 1e-12,
+            "l2": "inputs (57 MB) fit in L2: a 256 MiB buffer is written between steps"}
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = _rank_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from synth.configs import CONFIGS, load_mechanism, reactor_states
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize()
+
+    cfg = CONFIGS[WORKLOAD]
+    m = load_mechanism(cfg["mech"])
+    gm = ck.load_mechanism(m)
+    work = ck.count_work(gm)
+    N = cfg["n_reactors"]
+    y_np, p_np = reactor_states(WORKLOAD, n=N, seed_offset=1000 * rank)
+    dev = torch.device("cuda", torch.cuda.current_device())
+    y0 = torch.as_tensor(y_np, device=dev)
+    p = torch.as_tensor(p_np, device=dev)
+    dt = torch.full((N,), cfg["dt"], dtype=torch.float64, device=dev)
+    y_ros = torch.empty_like(y0)
+    y_rk = torch.empty_like(y0)
+    f = torch.empty_like(y0)
+    st_ros = torch.empty(N, dtype=torch.int32, device=dev)
+    st_rk = torch.empty(N, dtype=torch.int32, device=dev)
+    steps_ros = torch.empty((N, 2), dtype=torch.int32, device=dev)
+    steps_rk = torch.empty((N, 2), dtype=torch.int32, device=dev)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+    ev = {k: (torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for k in ("rhs", "ros4", "rkf45")}
+    dur = {k: [] for k in ev}
+
+    def step(record: bool):
+        flush.fill_(1.0)
+        y_ros.copy_(y0)
+        y_rk.copy_(y0)
+        ev["rhs"][0].record(stream)
+        ck.rhs(gm, p, y0, f, stream=stream)
+        ev["rhs"][1].record(stream)
+        ev["ros4"][0].record(stream)
+        ck.integrate_ros4(gm, p, y_ros, dt, st_ros, steps=steps_ros, stream=stream)
+        ev["ros4"][1].record(stream)
+        ev["rkf45"][0].record(stream)
+        ck.integrate_rkf45(gm, p, y_rk, dt, st_rk, steps=steps_rk, stream=stream)
+        ev["rkf45"][1].record(stream)
+        if record:
+            torch.cuda.synchronize()
+            for k, (a, b) in ev.items():
+                dur[k].append(a.elapsed_time(b) / 1e3)
+
+    for _ in range(args.warmup):
+        step(False)
+    barrier()
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for _ in range(args.steps):
+        step(True)
+    t1.record(stream)
+    barrier()
+    elapsed = t0.elapsed_time(t1) / 1e3
+    clocks = sampler.stop() if sampler else None
+    if world > 1:
+        tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    integrations = 2.0 * N * world * args.steps
+    value = integrations / elapsed
+
+    # correctness guard: every reactor finished
+    st_ok = int((st_ros == 0).sum().item()) == N and int((st_rk == 0).sum().item()) == N
+
+    # RHS throughput benchmark: repeats of the RHS over the batch
+    rhs_rate = None
+    if args.rhs_repeats > 0:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        a.record(stream)
+        for _ in range(args.rhs_repeats):
+            ck.rhs(gm, p, y0, f, stream=stream)
+        b.record(stream)
+        barrier()
+        rhs_rate = N * args.rhs_repeats / (a.elapsed_time(b) / 1e3)
+
+    # algorithmic FP64 work per launch (instructions; DFMA-equivalent flops = 2x)
+    sr = steps_ros.sum(dim=1).double()
+    sk = steps_rk.sum(dim=1).double()
+    ros_instr = float(sr.sum().item()) * work["ros4_step_fp64"] + 2 * N * work["rhs_fp64"]
+    rk_instr = float(sk.sum().item()) * work["rkf45_step_fp64"] + 2 * N * work["rhs_fp64"]
+    rhs_instr = N * work["rhs_fp64"]
+    mean = {k: float(np.mean(v)) for k, v in dur.items()}
+    instr = {"ros4": ros_instr, "rkf45": rk_instr, "rhs": rhs_instr}
+    kernel_names = {"ros4": "k_ros4", "rkf45": "k_rkf45", "rhs": "k_rhs"}
+    top = max(mean, key=mean.get)
+    achieved = 2.0 * instr[top] / mean[top] / 1e12
+    traffic = _traffic_for(kernel_names[top])
+    roofline = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic, "kernel": kernel_names[top],
+                "note": "FP64 pipe bound; flops = 2 x FP64 instructions of the algorithm "
+                        "(DFMA-equivalent); peak = nominal FP64 of the recipe (1.25 TFLOP/s); a DFMA "
+                        "probe measured 1.20 TFLOP/s"}
+    breakdown = {k: {"ms": 1e3 * mean[k], "tflops_dfma_eq": 2.0 * instr[k] / mean[k] / 1e12,
+                     "frac_of_fp64_peak": 2.0 * instr[k] / mean[k] / 1e12 / FP64_PEAK_TFLOPS}
+                 for k in mean}
+    breakdown["ros4"]["integrations_per_s"] = N / mean["ros4"]
+    breakdown["rkf45"]["integrations_per_s"] = N / mean["rkf45"]
+    breakdown["ros4"]["steps_mean"] = float(sr.mean().item())
+    breakdown["ros4"]["steps_max"] = int(sr.max().item())
+    breakdown["rkf45"]["steps_mean"] = float(sk.mean().item())
+    breakdown["rkf45"]["steps_max"] = int(sk.max().item())
+
+    # end to end through the C ABI with host buffers (the library stages)
+    e2e = None
+    if args.e2e_steps > 0:
+        yh = np.ascontiguousarray(y_np)
+        ph = np.ascontiguousarray(p_np)
+        dth = np.full(N, cfg["dt"])
+        fh = np.empty_like(yh)
+        sth = np.empty(N, np.int32)
+        h2d = d2h = 0
+        barrier()
+        te = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            ck.rhs(gm, ph, yh, fh)
+            h2d += ph.nbytes + yh.nbytes
+            d2h += fh.nbytes
+            for fn in (ck.integrate_ros4, ck.integrate_rkf45):
+                yw = yh.copy()
+                fn(gm, ph, yw, dth, sth)
+                h2d += ph.nbytes + yw.nbytes + dth.nbytes
+                d2h += yw.nbytes + sth.nbytes
+        barrier()
+        te = time.perf_counter() - te
+        e2e = {"value": 2.0 * N * world * args.e2e_steps / te, "unit": UNIT,
+               "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
+               "steps": args.e2e_steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and args.cpu_sample > 0:
+        cpu = cpu_baseline(args.cpu_sample)
+        cpu.pop("seconds", None)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * elapsed / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic (seeded stand-ins for the paper's GRI-Mech 3.0-sized mechanism and "
+                        "reactor states)",
+                "config": _config_dict(cfg), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": 3 * args.steps, "clocks": clocks,
+                "rhs_evals_per_s": rhs_rate, "rhs_repeats": args.rhs_repeats, "breakdown": breakdown,
+                "all_reactors_ok": st_ok}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+def run_profile_case(args):
+    """A small case of one kernel for ncu (warm-up launches, then 3 launches)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from synth.configs import CONFIGS, load_mechanism, reactor_states
+    cfg = CONFIGS[WORKLOAD]
+    gm = ck.load_mechanism(load_mechanism(cfg["mech"]))
+    N = args.reactors
+    y_np, p_np = reactor_states(WORKLOAD, n=N)
+    y0 = torch.as_tensor(y_np, device="cuda")
+    p = torch.as_tensor(p_np, device="cuda")
+    dt = torch.full((N,), args.dt or cfg["dt"], dtype=torch.float64, device="cuda")
+    y = torch.empty_like(y0)
+    st = torch.empty(N, dtype=torch.int32, device="cuda")
+    for _ in range(args.warmup + args.steps):
+        y.copy_(y0)
+        if args.profile_case == "ros4":
+            ck.integrate_ros4(gm, p, y, dt, st)
+        elif args.profile_case == "rkf45":
+            ck.integrate_rkf45(gm, p, y, dt, st)
+        else:
+            ck.rhs(gm, p, y0, y)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_case": args.profile_case, "reactors": N, "launches": args.warmup + args.steps,
+                      "ok": bool((st == 0).all().item()) if args.profile_case != "rhs" else True}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--rhs-repeats", type=int, default=1000)
+    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--cpu-sample", type=int, default=128)
+    ap.add_argument("--profile-case", choices=["ros4", "rkf45", "rhs"], default=None,
+                    help="profiling only: launch one kernel a few times on a small batch, print no bench line")
+    ap.add_argument("--reactors", type=int, default=2048, help="batch size of --profile-case")
+    ap.add_argument("--dt", type=float, default=None, help="dt of --profile-case (default: the workload's)")
+    args = ap.parse_args()
+    if args.profile_case:
+        run_profile_case(args)
+    elif args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

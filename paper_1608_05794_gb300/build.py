@@ -34,6 +34,16 @@ def sources() -> list[str]:
     return sorted(os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cu"))
 
 
+def sources_digest() -> str:
+    """SHA-256 over the CUDA sources and the public header (identifies a kernel build)."""
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(_deps()):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def _deps() -> list[str]:
     out = []
     for d in (CSRC, INCLUDE):
