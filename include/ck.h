@@ -179,6 +179,31 @@ int ck_integrate_rkf45(const ck_mech* mech, int64_t n, const double* p, double* 
                        double* h_inout, const ck_solver_opts* opts, int32_t* steps, int32_t* status,
                        void* stream);
 
+/* Allocation-free variant of ck_integrate_ros4 (no counterpart in the paper).
+ * Same arguments, arithmetic and results as ck_integrate_ros4, for callers
+ * that cannot let a library allocate device memory: a CFD code that hands
+ * all device memory to its own pool at start-up and runs with no headroom,
+ * or a process under a fixed device-memory budget where an allocation in the
+ * middle of a time step could fail.  ck_integrate_ros4 takes its work-queue
+ * counter from a per-call stream-ordered allocation; this entry point uses
+ * a statically allocated 256-byte device array instead (held on every GPU
+ * that loads the library until the process exits) and calls no cudaMalloc,
+ * cudaMallocAsync or cudaFree.
+ *   - Every array must be a device pointer; host arrays are rejected with
+ *     CK_EINVAL because staging them would need device buffers.
+ *   - n must not exceed CK_NOALLOC_MAX_REACTORS (CK_ERANGE otherwise).
+ *   - The first call on a device looks up the array's device address (once
+ *     per device, with that device current); make that first call before
+ *     any stream capture.
+ *   - All calls on a device share the array: the counter is zeroed on
+ *     `stream` before each launch, so calls that overlap on the GPU (on
+ *     different streams, or from several host threads) race and must be
+ *     serialized by the caller. */
+#define CK_NOALLOC_MAX_REACTORS (1LL << 30)
+int ck_integrate_ros4_noalloc(const ck_mech* mech, int64_t n, const double* p, double* y,
+                              const double* dt, double* h_inout, const ck_solver_opts* opts,
+                              int32_t* steps, int32_t* status, void* stream);
+
 /* Algorithmic FP64 work, counted from the loaded tables, in FP64 pipe
  * instructions (an FMA, a multiply, an add and a divide count one each; a
  * 2^x counts 8, the cost of the table-driven evaluation this library uses):

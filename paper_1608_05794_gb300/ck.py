@@ -18,7 +18,7 @@ from .build import LIB, build
 
 __all__ = [
     "Mechanism", "load_mechanism", "rhs", "jacobian", "lu_factor", "lu_solve", "integrate_ros4",
-    "integrate_rkf45", "count_work", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
+    "integrate_rkf45", "integrate_ros4_noalloc", "count_work", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
 ]
 
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "HMIN", 3: "NONFINITE", 4: "SINGULAR", 5: "BADINPUT"}
@@ -73,6 +73,8 @@ def _bind():
     L.ck_lu_solve.argtypes = [C.c_int64, C.c_int32, _DP, _DP, _DP, _DP]
     for f in (L.ck_integrate_ros4, L.ck_integrate_rkf45):
         f.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, _DP, C.POINTER(SolverOpts), _DP, _DP, _DP]
+    L.ck_integrate_ros4_noalloc.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, _DP, C.POINTER(SolverOpts), _DP,
+                                            _DP, _DP]
     L.ck_count_work.argtypes = [C.c_void_p, C.POINTER(WorkCounts)]
     L.ck_device_errors.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]
     L.ck_status_str.restype = C.c_char_p
@@ -226,6 +228,13 @@ def integrate_rkf45(mech, p, y, dt, status, h_inout=None, steps=None, opts=None,
     """RKF45 over [0, dt] for every reactor, in place on y (ck_integrate_rkf45)."""
     _integrate(_lib.ck_integrate_rkf45, "ck_integrate_rkf45", mech, p, y, dt, status, h_inout, steps, opts,
                stream)
+
+
+def integrate_ros4_noalloc(mech, p, y, dt, status, h_inout=None, steps=None, opts=None, stream=None):
+    """ROS4 without any device allocation (ck_integrate_ros4_noalloc): device
+    tensors only; calls on one device must not overlap on the GPU."""
+    _integrate(_lib.ck_integrate_ros4_noalloc, "ck_integrate_ros4_noalloc", mech, p, y, dt, status, h_inout,
+               steps, opts, stream)
 
 
 def count_work(mech: Mechanism) -> dict:

@@ -580,6 +580,38 @@ int ck_integrate_rkf45(const ck_mech* m, int64_t n, const double* p, double* y, 
   return integrate(1, m, n, p, y, dt, h_inout, opts, steps, status, stream);
 }
 
+int ck_integrate_ros4_noalloc(const ck_mech* m, int64_t n, const double* p, double* y,
+                              const double* dt, double* h_inout, const ck_solver_opts* opts,
+                              int32_t* steps, int32_t* status, void* stream) {
+  if (!m) return fail(CK_EINVAL, "mech is NULL");
+  if (n < 0) return fail(CK_EINVAL, "n < 0");
+  if (n > CK_NOALLOC_MAX_REACTORS)
+    return fail(CK_ERANGE, "ck_integrate_ros4_noalloc: n = " + std::to_string(n) +
+                               " exceeds CK_NOALLOC_MAX_REACTORS (" +
+                               std::to_string((long long)CK_NOALLOC_MAX_REACTORS) +
+                               "); split the batch or use ck_integrate_ros4");
+  if (n == 0) return CK_OK;
+  if (!p || !y || !dt || !status) return fail(CK_EINVAL, "p, y, dt and status are required");
+  if (is_host_ptr(p) || is_host_ptr(y) || is_host_ptr(dt) || is_host_ptr(h_inout) ||
+      is_host_ptr(steps) || is_host_ptr(status))
+    return fail(CK_EINVAL,
+                "ck_integrate_ros4_noalloc takes device pointers only: host arrays would need "
+                "device staging buffers, which this entry point does not allocate");
+  ck_solver_opts o;
+  if (opts) o = *opts;
+  else ck_default_opts(&o);
+  if (!(o.rtol > 0.0) || !(o.atol > 0.0) || o.max_steps < 1 || !(o.h0 >= 0.0) || !(o.fixed_h >= 0.0))
+    return fail(CK_EINVAL, "opts: need rtol > 0, atol > 0, max_steps >= 1, h0 >= 0, fixed_h >= 0");
+  if (o.precision != 0) return fail(CK_EINVAL, "opts.precision: only 0 (FP64) is available");
+  if (int rc = check_device(m)) return rc;
+  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
+  ck::LaunchCfg cfg;
+  if (o.variant > 0) cfg.team_warps = o.variant;
+  cudaError_t e = ck::launch_ros4_noalloc(m->hm, n, p, y, dt, h_inout, sp, steps, status,
+                                         static_cast<cudaStream_t>(stream), cfg);
+  return e == cudaSuccess ? CK_OK : cuda_fail(e, "ck_integrate_ros4_noalloc");
+}
+
 int ck_count_work(const ck_mech* m, ck_work_counts* o) {
   if (!m || !o) return fail(CK_EINVAL, "mech and out are required");
   const ck::HostMech& hm = m->hm;

@@ -54,4 +54,14 @@ cudaError_t launch_rkf45(const HostMech& hm, int64_t n, const double* p, double*
 
 int sm_count();
 
+// Allocation-free ROS4 (ck_integrate_ros4_noalloc): the work-queue counter
+// lives in a static device array of NOALLOC_SCRATCH_INTS ints.
+constexpr int NOALLOC_SCRATCH_INTS = 64;
+constexpr int NOALLOC_MAX_DEVICES = 64;
+cudaError_t noalloc_scratch(int32_t** out);
+cudaError_t launch_ros4_noalloc(const HostMech& hm, int64_t n, const double* p, double* y,
+                                const double* dt, double* h_io, const SolverParams& sp,
+                                int32_t* steps, int32_t* status, cudaStream_t st,
+                                const LaunchCfg& cfg);
+
 }  // namespace ck

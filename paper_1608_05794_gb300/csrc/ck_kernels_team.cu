@@ -5,6 +5,8 @@
 // atomic counter (dynamic scheduling, granularity one reactor).
 #include <cuda_runtime.h>
 
+#include <mutex>
+
 #include "ck_internal.h"
 #include "ck_team.cuh"
 
@@ -367,6 +369,48 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
   if (e != cudaSuccess) return e;
   k_ros4<<<grid, threads, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
   return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------ allocation-free ROS4
+// Scratch of ck_integrate_ros4_noalloc: the work-queue counter that
+// launch_ros4 otherwise receives from a per-call stream-ordered allocation.
+// Every GPU that loads the library holds these 256 bytes until the process
+// exits; all calls on a device share them.
+static __device__ __align__(256) int32_t g_noalloc_scratch[NOALLOC_SCRATCH_INTS];
+
+namespace {
+std::mutex g_noalloc_mu;
+int32_t* g_noalloc_ptr[NOALLOC_MAX_DEVICES] = {};
+}  // namespace
+
+// Device address of g_noalloc_scratch on the current device.  The name is
+// only a host-side stand-in, so the address is looked up once per device,
+// with that device current, and cached.
+cudaError_t noalloc_scratch(int32_t** out) {
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= NOALLOC_MAX_DEVICES) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_ptr[dev] = static_cast<int32_t*>(p);
+  }
+  *out = g_noalloc_ptr[dev];
+  return cudaSuccess;
+}
+
+cudaError_t launch_ros4_noalloc(const HostMech& hm, int64_t n, const double* p, double* y,
+                                const double* dt, double* h_io, const SolverParams& sp,
+                                int32_t* steps, int32_t* status, cudaStream_t st,
+                                const LaunchCfg& cfg) {
+  int32_t* queue = nullptr;
+  cudaError_t e = noalloc_scratch(&queue);
+  if (e != cudaSuccess) return e;
+  // launch_ros4 zeroes the counter on the stream before the kernel starts
+  return launch_ros4(hm, n, p, y, dt, h_io, sp, steps, status, queue, st, cfg);
 }
 
 }  // namespace ck
