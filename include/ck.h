@@ -119,7 +119,7 @@ typedef struct {
   double fixed_h;   /* > 0: constant step, no error control (order tests) */
   int32_t max_steps;/* attempted steps per reactor (accepted + rejected) */
   int32_t precision;/* 0: FP64 throughout */
-  int32_t variant;  /* 0: default launch shape; > 0: warps per reactor team */
+  int32_t variant;  /* 0: as many resident CTAs (ROS4) / blocks (RKF45) per SM as fit; > 0: cap per SM */
   int32_t reserved;
 } ck_solver_opts;
 

@@ -3,6 +3,7 @@
 // database" of Sec. 5), host/device pointer handling, launches.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -191,12 +192,26 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   const int S = d->n_species, R = d->n_reactions;
   const long double ln2 = 0.693147180559945309417232121458176568L;
   const long double Rg = 8.314462618L;
-  // reactions
+  // reactions, sorted by class so that neighbouring lanes of the team
+  // kernels branch alike (the order of a sum over reactions changes only the
+  // rounding of wdot)
+  std::vector<int> order(R);
+  for (int i = 0; i < R; ++i) order[i] = i;
+  auto nside = [&](const int32_t* a, int i) {
+    int c = 0;
+    for (int s = 0; s < 3; ++s) c += a[i * 3 + s] >= 0;
+    return c;
+  };
+  auto key = [&](int i) {
+    return ((d->rtype[i] * 2 + d->reversible[i]) * 4 + nside(d->reac, i)) * 4 + nside(d->prod, i);
+  };
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
   std::vector<RxnRec> rx(R);
   std::vector<int16_t> eff_sp;
   std::vector<double> eff_m1;
-  for (int i = 0; i < R; ++i) {
-    RxnRec& r = rx[i];
+  for (int ii = 0; ii < R; ++ii) {
+    const int i = order[ii];
+    RxnRec& r = rx[ii];
     std::memset(&r, 0, sizeof(r));
     const double* a = d->arrh + i * 3;
     r.lA2 = (double)(std::log2((long double)a[0]));
@@ -220,6 +235,9 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
     r.nreac = (int8_t)nr;
     r.nprod = (int8_t)np;
     r.dnu = (int8_t)(np - nr);
+    r.dnu_d = (double)(np - nr);
+    r.nreac_d = (double)nr;
+    r.nprod_d = (double)np;
     r.eff_beg = (int16_t)eff_sp.size();
     if (r.type != 0) {
       for (int e = d->eff_ptr[i]; e < d->eff_ptr[i + 1]; ++e) {
@@ -254,19 +272,72 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   for (int k = 0; k < S; ++k) invW[k] = (double)(1.0L / (long double)d->mw[k]);
   std::vector<double> tab(256);
   for (int j = 0; j < 256; ++j) tab[j] = (double)std::exp2((long double)j / 256.0L);
-  // species -> (reaction, net nu)
+  // species -> (reaction, net nu), in the sorted reaction order
   std::vector<int32_t> csr_ptr(S + 1, 0), csr_rx;
+  std::vector<double> csr_nu;
   for (int k = 0; k < S; ++k) {
     csr_ptr[k] = (int32_t)csr_rx.size();
     for (int i = 0; i < R; ++i) {
       int nu = 0;
-      for (int s = 0; s < 3; ++s) {
-        nu += (d->prod[i * 3 + s] == k) - (d->reac[i * 3 + s] == k);
+      for (int s = 0; s < 3; ++s) nu += (rx[i].sp[3 + s] == k) - (rx[i].sp[s] == k);
+      if (nu != 0) {
+        csr_rx.push_back(i);
+        csr_nu.push_back((double)nu);
       }
-      if (nu != 0) csr_rx.push_back((i << 8) | (nu + 8));
     }
   }
   csr_ptr[S] = (int32_t)csr_rx.size();
+  // team kernels walk the reactions in chunks of the CTA size
+  const int chunk = (S + 1 <= 56) ? 64 : 256;
+  const int n_chunks = (R + chunk - 1) / chunk;
+  std::vector<int32_t> csr_cptr((size_t)S * (n_chunks + 1));
+  for (int k = 0; k < S; ++k) {
+    int e = csr_ptr[k];
+    for (int c = 0; c <= n_chunks; ++c) {
+      while (e < csr_ptr[k + 1] && csr_rx[e] < c * chunk) ++e;
+      csr_cptr[(size_t)k * (n_chunks + 1) + c] = (c == n_chunks) ? csr_ptr[k + 1] : e;
+    }
+  }
+  // Jacobian contributions, chunk by chunk: A[k][j] += nu_ki * P[i][slot] for
+  // every slot of reaction i holding species j (and nu_ki (eff_ij - 1) *
+  // P[i][6] for the third-body corrections), grouped by entry (k, j)
+  std::vector<int32_t> jc_ptr(1, 0), jc_idx, jc_cp(1, 0), con_pidx;
+  std::vector<double> con_coef;
+  for (int c = 0; c < n_chunks; ++c) {
+    std::vector<std::vector<std::pair<double, int32_t>>> ent((size_t)S * S);
+    for (int k = 0; k < S; ++k) {
+      for (int e = csr_cptr[(size_t)k * (n_chunks + 1) + c]; e < csr_cptr[(size_t)k * (n_chunks + 1) + c + 1];
+           ++e) {
+        const int i = csr_rx[e];
+        const int li = i - c * chunk;
+        const double nu = csr_nu[e];
+        const RxnRec& r = rx[i];
+        for (int s2 = 0; s2 < r.nreac; ++s2) ent[(size_t)k * S + r.sp[s2]].push_back({nu, li * JP + s2});
+        if (r.rev)
+          for (int s2 = 0; s2 < r.nprod; ++s2)
+            ent[(size_t)k * S + r.sp[3 + s2]].push_back({nu, li * JP + 3 + s2});
+        for (int q = r.eff_beg; q < r.eff_beg + r.eff_cnt; ++q)
+          ent[(size_t)k * S + eff_sp[q]].push_back({nu * eff_m1[q], li * JP + 6});
+      }
+    }
+    std::vector<int> order_e;
+    for (int e = 0; e < S * S; ++e)
+      if (!ent[e].empty()) order_e.push_back(e);
+    // longest lists first, so that lanes running the same iteration do
+    // similar amounts of work
+    std::stable_sort(order_e.begin(), order_e.end(),
+                     [&](int a, int b) { return ent[a].size() > ent[b].size(); });
+    for (int e : order_e) {
+      const int k = e / S, j = e % S;
+      jc_idx.push_back((1 + k) * (S + 1) + 1 + j);
+      for (auto& cc : ent[e]) {
+        con_coef.push_back(cc.first);
+        con_pidx.push_back(cc.second);
+      }
+      jc_cp.push_back((int32_t)con_coef.size());
+    }
+    jc_ptr.push_back((int32_t)jc_idx.size());
+  }
   // one blob: staged block first, then the team-only tables
   StageLayout L{};
   size_t off = 0;
@@ -286,6 +357,13 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   L.bytes = (uint32_t)off;
   const size_t off_csr_ptr = place(sizeof(int32_t) * (S + 1));
   const size_t off_csr_rx = place(sizeof(int32_t) * csr_rx.size());
+  const size_t off_csr_nu = place(sizeof(double) * csr_nu.size());
+  const size_t off_csr_cptr = place(sizeof(int32_t) * csr_cptr.size());
+  const size_t off_jc_ptr = place(sizeof(int32_t) * jc_ptr.size());
+  const size_t off_jc_idx = place(sizeof(int32_t) * jc_idx.size());
+  const size_t off_jc_cp = place(sizeof(int32_t) * jc_cp.size());
+  const size_t off_con_coef = place(sizeof(double) * con_coef.size());
+  const size_t off_con_pidx = place(sizeof(int32_t) * con_pidx.size());
   const size_t off_err = place(sizeof(int32_t) * 4);
   const size_t total = off;
   std::vector<unsigned char> host(total, 0);
@@ -302,6 +380,13 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   put(L.tab, tab.data(), sizeof(double) * 256);
   put(off_csr_ptr, csr_ptr.data(), sizeof(int32_t) * (S + 1));
   put(off_csr_rx, csr_rx.data(), sizeof(int32_t) * csr_rx.size());
+  put(off_csr_nu, csr_nu.data(), sizeof(double) * csr_nu.size());
+  put(off_csr_cptr, csr_cptr.data(), sizeof(int32_t) * csr_cptr.size());
+  put(off_jc_ptr, jc_ptr.data(), sizeof(int32_t) * jc_ptr.size());
+  put(off_jc_idx, jc_idx.data(), sizeof(int32_t) * jc_idx.size());
+  put(off_jc_cp, jc_cp.data(), sizeof(int32_t) * jc_cp.size());
+  put(off_con_coef, con_coef.data(), sizeof(double) * con_coef.size());
+  put(off_con_pidx, con_pidx.data(), sizeof(int32_t) * con_pidx.size());
 
   ck_mech* m = new ck_mech;
   HostMech& hm = m->hm;
@@ -343,6 +428,17 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   dm.tab = reinterpret_cast<const double*>(b + L.tab);
   dm.csr_ptr = reinterpret_cast<const int32_t*>(b + off_csr_ptr);
   dm.csr_rx = reinterpret_cast<const int32_t*>(b + off_csr_rx);
+  dm.csr_nu = reinterpret_cast<const double*>(b + off_csr_nu);
+  dm.chunk = chunk;
+  dm.n_chunks = n_chunks;
+  dm.csr_cptr = reinterpret_cast<const int32_t*>(b + off_csr_cptr);
+  dm.jc_ptr = reinterpret_cast<const int32_t*>(b + off_jc_ptr);
+  dm.jc_idx = reinterpret_cast<const int32_t*>(b + off_jc_idx);
+  dm.jc_cp = reinterpret_cast<const int32_t*>(b + off_jc_cp);
+  dm.con_coef = reinterpret_cast<const double*>(b + off_con_coef);
+  dm.con_pidx = reinterpret_cast<const int32_t*>(b + off_con_pidx);
+  hm.n_contrib = (int)con_coef.size();
+  hm.csr_nnz = (int)csr_rx.size();
   hm.dev_err = reinterpret_cast<int32_t*>(b + off_err);
   *out = m;
   return CK_OK;
@@ -478,7 +574,7 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
   if (int rc = check_device(m)) return rc;
   ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
   ck::LaunchCfg cfg;
-  if (o.variant > 0) cfg.team_warps = o.variant;
+  if (o.variant > 0) cfg.ctas_per_sm = o.variant;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = (size_t)m->hm.d.n;
   const bool host = is_host_ptr(p) || is_host_ptr(y) || is_host_ptr(dt) || is_host_ptr(h_io) ||
@@ -536,26 +632,19 @@ double rhs_exps(const ck::HostMech& hm) {
 }
 double jac_count(const ck::HostMech& hm) {
   const double S = hm.S;
-  double c = 14.0 * S + 3.0 * S * S + S * S + 12.0 * S + 30.0;
+  // species pass extras (dcp), the species-block zeroing is not FP64,
+  // column sums S^2, transform 3 S^2, temperature row / column 12 S, J00
+  double c = 4.0 * S + S * S + 3.0 * S * S + 12.0 * S + 30.0;
   for (const auto& r : hm.rx) {
-    double per = 4 + 2 + 1 + 4 + 6 + 1;
+    double per = 3 + 3 + 4 + 1 + 6 + 1;  // dlnkf, c k, w, D, dq/dT
     if (r.rev) per += (r.nreac + r.nprod) + 2;
-    if (r.type == 2) per += 6;
+    if (r.type == 2) per += 7;
+    per += (r.nreac == 2 ? 2 : (r.nreac == 3 ? 6 : 0));
+    if (r.rev) per += (r.nprod == 2 ? 2 : (r.nprod == 3 ? 6 : 1));
     c += per;
-    // row pass: each species with a nonzero net coefficient touches the
-    // reaction's slots (and efficiency list)
-    int species = 0;
-    for (int s = 0; s < 6; ++s) {
-      if (r.sp[s] < 0) continue;
-      bool dup = false;
-      for (int t = 0; t < s; ++t) dup |= (r.sp[t] == r.sp[s]);
-      if (!dup) ++species;
-    }
-    const double slots = (r.nreac == 1 ? 1 : (r.nreac == 2 ? 2 : 5)) +
-                         (r.rev ? (r.nprod == 1 ? 1 : (r.nprod == 2 ? 2 : 5)) : 0) + 2 +
-                         (r.type ? r.eff_cnt + 2 : 0);
-    c += species * (3 + slots);
   }
+  c += hm.n_contrib;          // one FMA per contribution
+  c += 3.0 * hm.csr_nnz;      // aT, E, u (wdot is counted in the RHS)
   return c;
 }
 double lu_count(int n) {
@@ -606,7 +695,7 @@ int ck_integrate_ros4_noalloc(const ck_mech* m, int64_t n, const double* p, doub
   if (int rc = check_device(m)) return rc;
   ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
   ck::LaunchCfg cfg;
-  if (o.variant > 0) cfg.team_warps = o.variant;
+  if (o.variant > 0) cfg.ctas_per_sm = o.variant;
   cudaError_t e = ck::launch_ros4_noalloc(m->hm, n, p, y, dt, h_inout, sp, steps, status,
                                          static_cast<cudaStream_t>(stream), cfg);
   return e == cudaSuccess ? CK_OK : cuda_fail(e, "ck_integrate_ros4_noalloc");

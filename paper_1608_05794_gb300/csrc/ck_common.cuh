@@ -19,8 +19,10 @@ constexpr double LN2 = 0.6931471805599453094;
 constexpr double INV_LN2 = 1.4426950408889634074;
 constexpr double LOG2_P0_OVER_R = 13.573007627848395117;  // log2(101325 / 8.314462618)
 
-// One reaction, 80 bytes, read uniformly by all lanes (thread-per-reactor
-// kernels) or by one lane per reaction (team kernels).
+// One reaction, 96 bytes, read uniformly by all lanes (thread-per-reactor
+// kernels) or by one lane per reaction (team kernels).  The loader sorts the
+// reactions by (type, reversible, reactant count, product count) so that
+// neighbouring lanes of a team kernel take the same branches.
 struct __align__(16) RxnRec {
   double lA2;    // log2 A (SI)
   double beta;   // temperature exponent
@@ -28,15 +30,22 @@ struct __align__(16) RxnRec {
   double lA02;   // Lindemann low-pressure limit: log2 A0
   double beta0;
   double E0oR2;
+  double dnu_d;    // sum of product minus reactant coefficients, as FP64
+  double nreac_d;  // reactant count, as FP64
+  double nprod_d;  // product count, as FP64
   int16_t sp[6];    // reactant slots 0..2, product slots 3..5, -1 padded
   int8_t type;      // 0 elementary, 1 third-body, 2 Lindemann
   int8_t rev;       // 1 reversible through K_c
-  int8_t dnu;       // sum of product minus reactant coefficients
+  int8_t dnu;
   int8_t nreac, nprod, pad0;
   int16_t eff_beg, eff_cnt;  // slice of the efficiency table (eff - 1 != 0)
-  int16_t pad1, pad2;
+  int16_t pad1;
 };
-static_assert(sizeof(RxnRec) == 80, "RxnRec layout");
+static_assert(sizeof(RxnRec) == 96, "RxnRec layout");
+
+// Jacobian partials stored per reaction: reactant slots 0..2, product slots
+// 3..5, and slot 6 = dc/d[M] * (k_f prod' - k_r prod'').
+constexpr int JP = 7;
 
 // Per species and temperature range: 18 doubles
 //   cp/R  : c0 + c1 T + c2 T^2 + c3 T^3 + c4 T^4               [0..4]
@@ -61,8 +70,23 @@ struct DevMech {
   const int16_t* eff_sp;  // [n_eff]
   const double* eff_m1;   // [n_eff] efficiency - 1
   const int32_t* csr_ptr; // [S+1] species -> (reaction, net nu) lists
-  const int32_t* csr_rx;  // [csr_nnz] reaction index << 8 | (nu + 8)
+  const int32_t* csr_rx;  // [csr_nnz] reaction index
+  const double* csr_nu;   // [csr_nnz] net stoichiometric coefficient
   const double* tab;      // [256] 2^(j/256)
+  // Team kernels walk the reactions in chunks of `chunk` (= CTA size).
+  // csr_cptr[k (n_chunks + 1) + c] = first CSR entry of species k whose
+  // reaction lies in chunk c or later.  Jacobian assembly, chunk c: the
+  // entries e in [jc_ptr[c], jc_ptr[c+1]) of the species block A (flat
+  // shared-memory index jc_idx[e]) add the sum over t in [jc_cp[e],
+  // jc_cp[e+1]) of con_coef[t] * P[con_pidx[t]] (P: the chunk's partials,
+  // JP per reaction).
+  int chunk, n_chunks;
+  const int32_t* csr_cptr;
+  const int32_t* jc_ptr;
+  const int32_t* jc_idx;
+  const int32_t* jc_cp;
+  const double* con_coef;
+  const int32_t* con_pidx;
 };
 
 // ---------------------------------------------------------------- 2^x

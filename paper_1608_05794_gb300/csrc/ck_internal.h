@@ -26,6 +26,7 @@ struct HostMech {
   // host copies used for work counting
   std::vector<RxnRec> rx;
   int S = 0, R = 0;
+  int n_contrib = 0, csr_nnz = 0;
 };
 
 // Device-side error bits reported through HostMech::dev_err.

@@ -6,15 +6,16 @@
 #include <cuda_runtime.h>
 
 #include <mutex>
+#include <type_traits>
 
 #include "ck_internal.h"
 #include "ck_team.cuh"
 
 namespace ck {
 
-__host__ __device__ __forceinline__ int team_bufs_doubles(int S, int R) { return 10 * S + 6 * R + 64; }
+__host__ __device__ __forceinline__ int team_bufs_doubles(int S, int chunk) { return 9 * S + (3 + JP) * chunk + 32; }
 
-__device__ __forceinline__ TeamBufs carve_bufs(double* base, int S, int R) {
+__device__ __forceinline__ TeamBufs carve_bufs(double* base, int S, int CH) {
   TeamBufs b;
   b.X = base;
   b.g2 = b.X + S;
@@ -25,14 +26,12 @@ __device__ __forceinline__ TeamBufs carve_bufs(double* base, int S, int R) {
   b.aT = b.wd + S;
   b.E = b.aT + S;
   b.u = b.E + S;
-  b.cs = b.u + S;
-  b.q = b.cs + S;
-  b.ckf = b.q + R;
-  b.ckr = b.ckf + R;
-  b.w = b.ckr + R;
-  b.dqT = b.w + R;
-  b.D = b.dqT + R;
-  b.red = b.D + R;
+  b.cs = b.g2;  // column sums reuse g2 (free after the reaction passes)
+  b.q = b.u + S;
+  b.dqT = b.q + CH;
+  b.D = b.dqT + CH;
+  b.P = b.D + CH;
+  b.red = b.P + (size_t)JP * CH;
   return b;
 }
 
@@ -53,7 +52,7 @@ __global__ void k_jacobian(DevMech d, int64_t N, const double* __restrict__ p,
   double* J = sm;
   double* ys = J + (size_t)n * n;
   double* fs = ys + n;
-  TeamBufs b = carve_bufs(fs + n, d.S, d.R);
+  TeamBufs b = carve_bufs(fs + n, d.S, d.chunk);
   Mix x;
   for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = y[r * n + i];
@@ -65,20 +64,22 @@ __global__ void k_jacobian(DevMech d, int64_t N, const double* __restrict__ p,
 }
 
 // ------------------------------------------------------------------ batched LU
-__global__ void k_lu_factor(int64_t batch, int dim, double* __restrict__ a, int32_t* __restrict__ piv,
-                            int32_t* __restrict__ info) {
+template <int G, int T>
+__global__ void __launch_bounds__(G * G, 1) k_lu_factor(int64_t batch, int dim, double* __restrict__ a,
+                                                      int32_t* __restrict__ piv, int32_t* __restrict__ info) {
   extern __shared__ __align__(16) double sm[];
   double* A = sm;
   double* invd = A + (size_t)dim * dim;
   int* pv = reinterpret_cast<int*>(invd + dim);
-  double* red = invd + 2 * dim;
+  double* lb = invd + 2 * dim;
+  double* ub = lb + dim;
+  double* red = ub + dim;
   const int64_t nn = (int64_t)dim * dim;
   for (int64_t m = blockIdx.x; m < batch; m += gridDim.x) {
     for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) A[e] = a[m * nn + e];
     for (int i = threadIdx.x; i < dim; i += blockDim.x) pv[i] = i;
     __syncthreads();
-    const int inf = team_lu(A, dim, pv, invd, red);
-    __syncthreads();
+    const int inf = lu_reg<G, T>(A, dim, pv, invd, lb, ub, red);
     for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) a[m * nn + e] = A[e];
     for (int i = threadIdx.x; i < dim; i += blockDim.x) piv[m * dim + i] = pv[i];
     if (threadIdx.x == 0) info[m] = inf;
@@ -103,7 +104,8 @@ __global__ void k_lu_solve(int64_t batch, int dim, const double* __restrict__ lu
     __syncthreads();
     for (int i = threadIdx.x; i < dim; i += blockDim.x) invd[i] = 1.0 / A[(size_t)i * dim + i];
     __syncthreads();
-    team_lu_solve(A, dim, pv, invd, x);
+    if (threadIdx.x < 32) warp_lu_solve(A, dim, pv, invd, x);
+    __syncthreads();
     for (int i = threadIdx.x; i < dim; i += blockDim.x) bvec[m * dim + i] = x[i];
     __syncthreads();
   }
@@ -125,10 +127,11 @@ __device__ __forceinline__ double team_wrms(int n, const double* e, const double
 }
 
 // Initial step, Hairer-Norsett-Wanner starting-step algorithm (order 4).
-__device__ double team_h0(const DevMech& d, double p, const double* y0, double tspan, double rtol,
-                          double atol, double* f0, double* y1, double* f1, TeamBufs& b, Mix& x) {
+__device__ double team_h0(const DevMech& d, const double* tab, double p, const double* y0, double tspan,
+                          double rtol, double atol, double* f0, double* y1, double* f1, TeamBufs& b,
+                          Mix& x) {
   const int n = d.n;
-  team_rhs(d, d.tab, p, y0, f0, b, x);
+  team_rhs(d, tab, p, y0, f0, b, x);
   double s0 = 0.0, s1 = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double sc = atol + rtol * fabs(y0[i]);
@@ -140,7 +143,7 @@ __device__ double team_h0(const DevMech& d, double p, const double* y0, double t
   const double ha = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
   for (int i = threadIdx.x; i < n; i += blockDim.x) y1[i] = fma(ha, f0[i], y0[i]);
   team_sync();
-  team_rhs(d, d.tab, p, y1, f1, b, x);
+  team_rhs(d, tab, p, y1, f1, b, x);
   double s2 = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double sc = atol + rtol * fabs(y0[i]);
@@ -153,12 +156,15 @@ __device__ double team_h0(const DevMech& d, double p, const double* y0, double t
   return fmin(fmin(100.0 * ha, hb), tspan);
 }
 
-__global__ void k_ros4(DevMech d, int64_t N, const double* __restrict__ p, double* __restrict__ y,
-                       const double* __restrict__ dt, double* h_io, SolverParams sp, int32_t* steps,
-                       int32_t* status, int32_t* queue) {
+template <int G, int T>
+__global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64_t N, const double* __restrict__ p,
+                                                 double* __restrict__ y, const double* __restrict__ dt,
+                                                 double* h_io, SolverParams sp, int32_t* steps,
+                                                 int32_t* status, int32_t* queue) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int slot;
   const int n = d.n;
+  const double* tab = d.tab;  // 2 KB, stays in L1
   double* M = sm;
   double* yv = M + (size_t)n * n;
   double* F0 = yv + n;
@@ -170,7 +176,9 @@ __global__ void k_ros4(DevMech d, int64_t N, const double* __restrict__ p, doubl
   double* u4 = u3 + n;
   double* invd = u4 + n;
   int* piv = reinterpret_cast<int*>(invd + n);
-  TeamBufs b = carve_bufs(invd + 2 * n, d.S, d.R);
+  double* lb = F;   // LU broadcast buffers: F and Yt are free while factoring
+  double* ub = Yt;
+  TeamBufs b = carve_bufs(invd + n + (n + 1) / 2, d.S, d.chunk);
   Mix x;
   const bool fixed = sp.fixed_h > 0.0;
   const int tid = threadIdx.x, P = blockDim.x;
@@ -193,7 +201,7 @@ __global__ void k_ros4(DevMech d, int64_t N, const double* __restrict__ p, doubl
       if (fixed) h = sp.fixed_h;
       else if (h_io && h_io[r] > 0.0) h = h_io[r];
       else if (sp.h0 > 0.0) h = sp.h0;
-      else h = team_h0(d, pr, yv, tf, sp.rtol, sp.atol, F0, Yt, F, b, x);
+      else h = team_h0(d, tab, pr, yv, tf, sp.rtol, sp.atol, F0, Yt, F, b, x);
       const double hmin = 1e-15 * tf;
       double t = 0.0;
       bool last_rej = false, last_nf = false;
@@ -204,13 +212,13 @@ __global__ void k_ros4(DevMech d, int64_t N, const double* __restrict__ p, doubl
         const double hh = clamped ? tf - t : h;
         if (hh < hmin) { st = last_nf ? ST_NONFINITE : ST_HMIN; break; }
         // J and f at y; M = I/(hh gamma) - J; LU
-        team_jacobian(d, d.tab, pr, yv, F0, M, b, x);
+        team_jacobian(d, tab, pr, yv, F0, M, b, x);
         const double dg = 1.0 / (hh * ROS_GAMMA);
         for (int e = tid; e < n * n; e += P) M[e] = -M[e];
         team_sync();
         for (int i = tid; i < n; i += P) M[(size_t)i * n + i] += dg;
         team_sync();
-        const int info = team_lu(M, n, piv, invd, b.red);
+        const int info = lu_reg<G, T>(M, n, piv, invd, lb, ub, b.red);
         if (info) {
           ++rej;
           if (++sing_run >= SINGULAR_LIMIT) { st = ST_SINGULAR; break; }
@@ -223,27 +231,31 @@ __global__ void k_ros4(DevMech d, int64_t N, const double* __restrict__ p, doubl
         // stage 1: M u1 = f(y)
         for (int i = tid; i < n; i += P) u1[i] = F0[i];
         team_sync();
-        team_lu_solve(M, n, piv, invd, u1);
+        if (tid < 32) warp_lu_solve(M, n, piv, invd, u1);
+        __syncthreads();
         // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
         for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A21, u1[i], yv[i]);
         team_sync();
-        team_rhs(d, d.tab, pr, Yt, F, b, x);
+        team_rhs(d, tab, pr, Yt, F, b, x);
         for (int i = tid; i < n; i += P) u2[i] = fma(ROS_C21 * ih, u1[i], F[i]);
         team_sync();
-        team_lu_solve(M, n, piv, invd, u2);
+        if (tid < 32) warp_lu_solve(M, n, piv, invd, u2);
+        __syncthreads();
         // stage 3: M u3 = f(y + a31 u1 + a32 u2) + (c31 u1 + c32 u2)/h
         for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A32, u2[i], fma(ROS_A31, u1[i], yv[i]));
         team_sync();
-        team_rhs(d, d.tab, pr, Yt, F, b, x);
+        team_rhs(d, tab, pr, Yt, F, b, x);
         for (int i = tid; i < n; i += P)
           u3[i] = fma(ROS_C32 * ih, u2[i], fma(ROS_C31 * ih, u1[i], F[i]));
         team_sync();
-        team_lu_solve(M, n, piv, invd, u3);
+        if (tid < 32) warp_lu_solve(M, n, piv, invd, u3);
+        __syncthreads();
         // stage 4: same argument as stage 3 (a4j = a3j, a43 = 0), so f is reused
         for (int i = tid; i < n; i += P)
           u4[i] = fma(ROS_C43 * ih, u3[i], fma(ROS_C42 * ih, u2[i], fma(ROS_C41 * ih, u1[i], F[i])));
         team_sync();
-        team_lu_solve(M, n, piv, invd, u4);
+        if (tid < 32) warp_lu_solve(M, n, piv, invd, u4);
+        __syncthreads();
         // y* = y + sum m_i u_i (into Yt), e = sum E_i u_i (into F)
         int nf = 0;
         for (int i = tid; i < n; i += P) {
@@ -320,16 +332,26 @@ static int team_grid(K kernel, int threads, size_t smem, int64_t work, const Lau
   return (int)(g < 1 ? 1 : g);
 }
 
-size_t ros4_smem_bytes(int n, int S, int R) {
-  return sizeof(double) * ((size_t)n * n + 11 * (size_t)n + team_bufs_doubles(S, R));
+size_t ros4_smem_bytes(int n, int S, int chunk) {
+  return sizeof(double) * ((size_t)n * n + 9 * (size_t)n + (n + 1) / 2 + team_bufs_doubles(S, chunk));
+}
+
+// Thread grid of the register-tiled LU for dimension n: G x G threads with
+// T x T tiles (n <= G T).
+template <class F>
+static cudaError_t with_grid(int n, F f) {
+  if (n <= 56) return f(std::integral_constant<int, 8>{}, std::integral_constant<int, 7>{});
+  if (n <= 112) return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 7>{});
+  if (n <= 144) return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 9>{});
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_jacobian(const HostMech& hm, int64_t n, const double* p, const double* y,
                             double* jac, cudaStream_t st, const LaunchCfg& cfg) {
   if (n <= 0) return cudaSuccess;
   const int nn = hm.d.n;
-  const size_t smem = sizeof(double) * ((size_t)nn * nn + 2 * nn + team_bufs_doubles(hm.S, hm.R));
-  const int threads = team_threads(nn, cfg);
+  const size_t smem = sizeof(double) * ((size_t)nn * nn + 2 * nn + team_bufs_doubles(hm.S, hm.d.chunk));
+  const int threads = hm.d.chunk;
   const int grid = team_grid(k_jacobian, threads, smem, n, cfg);
   k_jacobian<<<grid, threads, smem, st>>>(hm.d, n, p, y, jac);
   return cudaGetLastError();
@@ -338,12 +360,15 @@ cudaError_t launch_jacobian(const HostMech& hm, int64_t n, const double* p, cons
 cudaError_t launch_lu_factor(int64_t batch, int dim, double* a, int32_t* piv, int32_t* info,
                              cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * ((size_t)dim * dim + 2 * dim + 64);
+  const size_t smem = sizeof(double) * ((size_t)dim * dim + 4 * dim + 64);
   LaunchCfg cfg;
-  const int threads = team_threads(dim, cfg);
-  const int grid = team_grid(k_lu_factor, threads, smem, batch, cfg);
-  k_lu_factor<<<grid, threads, smem, st>>>(batch, dim, a, piv, info);
-  return cudaGetLastError();
+  return with_grid(dim, [&](auto Gc, auto Tc) {
+    constexpr int G = decltype(Gc)::value, T = decltype(Tc)::value;
+    auto kern = k_lu_factor<G, T>;
+    const int grid = team_grid(kern, G * G, smem, batch, cfg);
+    kern<<<grid, G * G, smem, st>>>(batch, dim, a, piv, info);
+    return cudaGetLastError();
+  });
 }
 
 cudaError_t launch_lu_solve(int64_t batch, int dim, const double* lu, const int32_t* piv,
@@ -362,13 +387,16 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
                         int32_t* queue, cudaStream_t st, const LaunchCfg& cfg) {
   if (n <= 0) return cudaSuccess;
   const int nn = hm.d.n;
-  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.R);
-  const int threads = team_threads(nn, cfg);
-  const int grid = team_grid(k_ros4, threads, smem, n, cfg);
+  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.d.chunk);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
-  k_ros4<<<grid, threads, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
-  return cudaGetLastError();
+  return with_grid(nn, [&](auto Gc, auto Tc) {
+    constexpr int G = decltype(Gc)::value, T = decltype(Tc)::value;
+    auto kern = k_ros4<G, T>;
+    const int grid = team_grid(kern, G * G, smem, n, cfg);
+    kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
+    return cudaGetLastError();
+  });
 }
 
 // ------------------------------------------------------------------ allocation-free ROS4

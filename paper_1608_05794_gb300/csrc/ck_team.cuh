@@ -35,10 +35,14 @@ __device__ __forceinline__ void team_sync() {
 }
 
 // Shared-memory work arrays of one team.
+// Reactions are processed in chunks of m.chunk (the CTA size), so the
+// per-reaction arrays hold one chunk; cs aliases g2 (free once the reaction
+// passes are done).
 struct TeamBufs {
   double *X, *g2, *hRT, *cpR, *dcpR, *wd, *aT, *E, *u, *cs;  // [S]
-  double *q, *ckf, *ckr, *w, *dqT, *D;                         // [R]
-  double* red;                                                // [64]
+  double *q, *dqT, *D;                                        // [chunk]
+  double* P;                                                  // [chunk * JP] Jacobian partials
+  double* red;                                                // [32]
 };
 
 // Mixture quantities shared by the RHS and the Jacobian.
@@ -77,6 +81,10 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
     b.cpR[k] = fma(a[4], x.T4, fma(a[3], x.T3, fma(a[2], x.T2, fma(a[1], x.T, a[0]))));
     b.hRT[k] = fma(a[10], x.invT, fma(a[9], x.T4, fma(a[8], x.T3, fma(a[7], x.T2, fma(a[6], x.T, a[5])))));
     if (want_dcp) b.dcpR[k] = fma(4.0 * a[4], x.T3, fma(3.0 * a[3], x.T2, fma(2.0 * a[2], x.T, a[1])));
+    b.wd[k] = 0.0;
+    b.aT[k] = 0.0;
+    b.E[k] = 0.0;
+    b.u[k] = 0.0;
   }
   x.Ctot = team_sum(c, b.red);
 }
@@ -86,6 +94,7 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
 __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r, const Mix& x,
                                               const TeamBufs& b, const double* tab, int i,
                                               bool want_jac) {
+  // i: index of the reaction inside the current chunk
   const double* X = b.X;
   const double* g2 = b.g2;
   const double l2kf = fma(-r.EoR2, x.invT, fma(r.beta, x.log2T, r.lA2));
@@ -95,7 +104,7 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
   if (r.nreac > 2) fwd *= X[r.sp[2]];
   double kr = 0.0, rv = 0.0, dlnkc = 0.0;
   if (r.rev) {
-    double l2kc = (double)r.dnu * (LOG2_P0_OVER_R - x.log2T);
+    double l2kc = r.dnu_d * (LOG2_P0_OVER_R - x.log2T);
     l2kc += g2[r.sp[3]];
     if (r.nprod > 1) l2kc += g2[r.sp[4]];
     if (r.nprod > 2) l2kc += g2[r.sp[5]];
@@ -114,7 +123,7 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
       hs -= b.hRT[r.sp[0]];
       if (r.nreac > 1) hs -= b.hRT[r.sp[1]];
       if (r.nreac > 2) hs -= b.hRT[r.sp[2]];
-      dlnkc = (hs - (double)r.dnu) * x.invT;
+      dlnkc = (hs - r.dnu_d) * x.invT;
     }
   }
   const double net = fma(-kr, rv, kf * fwd);
@@ -143,13 +152,42 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
   b.q[i] = q;
   if (want_jac) {
     const double ckf = c * kf, ckr = c * kr;
-    b.ckf[i] = ckf;
-    b.ckr[i] = ckr;
     const double w = dcdM * net;
-    b.w[i] = w;
+    // d q / d[X] slot by slot: c k_f prod of the other reactant slots, and
+    // -c k_r prod of the other product slots
+    double* P = b.P + (size_t)i * JP;
+    const double x0 = X[r.sp[0]];
+    if (r.nreac == 1) {
+      P[0] = ckf;
+    } else if (r.nreac == 2) {
+      const double x1 = X[r.sp[1]];
+      P[0] = ckf * x1;
+      P[1] = ckf * x0;
+    } else {
+      const double x1 = X[r.sp[1]], x2 = X[r.sp[2]];
+      P[0] = ckf * (x1 * x2);
+      P[1] = ckf * (x0 * x2);
+      P[2] = ckf * (x0 * x1);
+    }
+    if (r.rev) {
+      const double y0 = X[r.sp[3]];
+      if (r.nprod == 1) {
+        P[3] = -ckr;
+      } else if (r.nprod == 2) {
+        const double y1 = X[r.sp[4]];
+        P[3] = -ckr * y1;
+        P[4] = -ckr * y0;
+      } else {
+        const double y1 = X[r.sp[4]], y2 = X[r.sp[5]];
+        P[3] = -ckr * (y1 * y2);
+        P[4] = -ckr * (y0 * y2);
+        P[5] = -ckr * (y0 * y1);
+      }
+    }
+    P[6] = w;
     // D = sum_j dq/d[X_j] [X_j]: Euler's theorem for the mass-action
     // products (homogeneous of degree nreac / nprod) plus the [M] part.
-    const double D = fma(ckf * fwd, (double)r.nreac, -(ckr * rv) * (double)r.nprod) + M * w;
+    const double D = fma(ckf * fwd, r.nreac_d, -(ckr * rv) * r.nprod_d) + M * w;
     b.D[i] = D;
     // dq/dT at fixed [X], then the total derivative at fixed Y (d[X]/dT = -[X]/T)
     const double dqTX = fma(dcdT, net, ckf * fwd * dlnkf - ckr * rv * (dlnkf - dlnkc));
@@ -158,21 +196,28 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
 }
 
 // f(y) for one reactor.  y, f: shared memory, n = S + 1.
-__device__ void team_rhs(const DevMech& m, const double* tab, double p, const double* y, double* f,
+static __device__ void team_rhs(const DevMech& m, const double* tab, double p, const double* y, double* f,
                          TeamBufs& b, Mix& x) {
   team_species(m, p, y, b, x, false);
   team_sync();
-  for (int i = threadIdx.x; i < m.R; i += blockDim.x) team_reaction(m, m.rxn[i], x, b, tab, i, false);
-  team_sync();
+  const int NC = m.n_chunks, CH = m.chunk;
+  for (int c = 0; c < NC; ++c) {
+    const int base = c * CH;
+    for (int li = threadIdx.x; li < CH; li += blockDim.x)
+      if (base + li < m.R) team_reaction(m, m.rxn[base + li], x, b, tab, li, false);
+    team_sync();
+    for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
+      const int* cp = m.csr_cptr + k * (NC + 1) + c;
+      double w = b.wd[k];
+      for (int e = cp[0]; e < cp[1]; ++e) w = fma(m.csr_nu[e], b.q[m.csr_rx[e] - base], w);
+      b.wd[k] = w;
+    }
+    team_sync();
+  }
   const double invrho = 1.0 / x.rho;
   double cpm = 0.0, hw = 0.0;
   for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
-    double w = 0.0;
-    for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) {
-      const int32_t code = m.csr_rx[e];
-      w = fma((double)((code & 255) - 8), b.q[code >> 8], w);
-    }
-    b.wd[k] = w;
+    const double w = b.wd[k];
     cpm = fma(y[1 + k] * m.invW[k], b.cpR[k], cpm);
     hw = fma(b.hRT[k], w, hw);
     f[1 + k] = w * (m.W[k] * invrho);
@@ -195,70 +240,48 @@ __device__ void team_rhs(const DevMech& m, const double* tab, double p, const do
 //   J[0][0]     = -(sum cp_k wdot_k + T sum H_k/RT a_k)/(rho cpm) - Tdot (dcpm/cpm - 1/T),
 // with cs_j = sum_k H_k/RT (A_kj + u_k), HE = sum_k H_k/RT E_k, and heat
 // capacities in units of R.
-__device__ void team_jacobian(const DevMech& m, const double* tab, double p, const double* y,
+static __device__ void team_jacobian(const DevMech& m, const double* tab, double p, const double* y,
                               double* f, double* J, TeamBufs& b, Mix& x) {
   const int S = m.S, n = m.n;
   team_species(m, p, y, b, x, true);
-  team_sync();
-  for (int i = threadIdx.x; i < m.R; i += blockDim.x) team_reaction(m, m.rxn[i], x, b, tab, i, true);
-  team_sync();
-  // row pass: each thread owns whole species rows of A (no write conflicts)
-  for (int k = threadIdx.x; k < S; k += blockDim.x) {
-    double* row = J + (size_t)(1 + k) * n + 1;
-    for (int j = 0; j < S; ++j) row[j] = 0.0;
-    double w = 0.0, aT = 0.0, E = 0.0, u = 0.0;
-    for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) {
-      const int32_t code = m.csr_rx[e];
-      const int i = code >> 8;
-      const double nu = (double)((code & 255) - 8);
-      const RxnRec& r = m.rxn[i];
-      w = fma(nu, b.q[i], w);
-      aT = fma(nu, b.dqT[i], aT);
-      E = fma(nu, b.D[i], E);
-      // d(prod [X]^nu')/d[X_s] slot by slot
-      const double cf = nu * b.ckf[i];
-      const double x0 = b.X[r.sp[0]];
-      if (r.nreac == 1) {
-        row[r.sp[0]] += cf;
-      } else if (r.nreac == 2) {
-        const double x1 = b.X[r.sp[1]];
-        row[r.sp[0]] = fma(cf, x1, row[r.sp[0]]);
-        row[r.sp[1]] = fma(cf, x0, row[r.sp[1]]);
-      } else {
-        const double x1 = b.X[r.sp[1]], x2 = b.X[r.sp[2]];
-        row[r.sp[0]] = fma(cf, x1 * x2, row[r.sp[0]]);
-        row[r.sp[1]] = fma(cf, x0 * x2, row[r.sp[1]]);
-        row[r.sp[2]] = fma(cf, x0 * x1, row[r.sp[2]]);
-      }
-      if (r.rev) {
-        const double cr = -nu * b.ckr[i];
-        const double y0 = b.X[r.sp[3]];
-        if (r.nprod == 1) {
-          row[r.sp[3]] += cr;
-        } else if (r.nprod == 2) {
-          const double y1 = b.X[r.sp[4]];
-          row[r.sp[3]] = fma(cr, y1, row[r.sp[3]]);
-          row[r.sp[4]] = fma(cr, y0, row[r.sp[4]]);
-        } else {
-          const double y1 = b.X[r.sp[4]], y2 = b.X[r.sp[5]];
-          row[r.sp[3]] = fma(cr, y1 * y2, row[r.sp[3]]);
-          row[r.sp[4]] = fma(cr, y0 * y2, row[r.sp[4]]);
-          row[r.sp[5]] = fma(cr, y0 * y1, row[r.sp[5]]);
-        }
-      }
-      if (r.type) {
-        const double nw = nu * b.w[i];
-        u += nw;
-        for (int e2 = r.eff_beg; e2 < r.eff_beg + r.eff_cnt; ++e2)
-          row[m.eff_sp[e2]] = fma(nw, m.eff_m1[e2], row[m.eff_sp[e2]]);
-      }
-    }
-    b.wd[k] = w;
-    b.aT[k] = aT;
-    b.E[k] = E;
-    b.u[k] = u;
+  // species block A starts at zero; chunk by chunk, every entry touched by
+  // the chunk adds its fixed-order sum of contributions (one thread per
+  // entry, no conflicts), and every species adds its terms of wdot,
+  // d wdot/dT, E = sum nu D and the dense third-body part u
+  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
+    const int k = e / S, j = e - k * S;
+    J[(size_t)(1 + k) * n + 1 + j] = 0.0;
   }
   team_sync();
+  const int NC = m.n_chunks, CH = m.chunk;
+  for (int c = 0; c < NC; ++c) {
+    const int base = c * CH;
+    for (int li = threadIdx.x; li < CH; li += blockDim.x)
+      if (base + li < m.R) team_reaction(m, m.rxn[base + li], x, b, tab, li, true);
+    team_sync();
+    for (int e = m.jc_ptr[c] + threadIdx.x; e < m.jc_ptr[c + 1]; e += blockDim.x) {
+      double a = J[m.jc_idx[e]];
+      for (int t = m.jc_cp[e]; t < m.jc_cp[e + 1]; ++t) a = fma(m.con_coef[t], b.P[m.con_pidx[t]], a);
+      J[m.jc_idx[e]] = a;
+    }
+    for (int k = threadIdx.x; k < S; k += blockDim.x) {
+      const int* cp = m.csr_cptr + k * (NC + 1) + c;
+      double w = b.wd[k], aT = b.aT[k], E = b.E[k], u = b.u[k];
+      for (int e = cp[0]; e < cp[1]; ++e) {
+        const int li = m.csr_rx[e] - base;
+        const double nu = m.csr_nu[e];
+        w = fma(nu, b.q[li], w);
+        aT = fma(nu, b.dqT[li], aT);
+        E = fma(nu, b.D[li], E);
+        u = fma(nu, b.P[(size_t)li * JP + 6], u);
+      }
+      b.wd[k] = w;
+      b.aT[k] = aT;
+      b.E[k] = E;
+      b.u[k] = u;
+    }
+    team_sync();
+  }
   // column sums for the temperature row, and the RHS itself
   const double invrho = 1.0 / x.rho;
   double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = 0.0, cw = 0.0, ha = 0.0;
@@ -308,98 +331,239 @@ __device__ void team_jacobian(const DevMech& m, const double* tab, double p, con
   team_sync();
 }
 
-// In-place LU with partial pivoting of the n x n row-major matrix A
-// (shared memory).  piv[k] = row swapped with row k; the inverse pivots go
-// to invd.  Returns 0, or k+1 when pivot k is zero or not finite (the value
-// is the same in every thread).  Ties pick the smallest row index.
-__device__ int team_lu(double* A, int n, int* piv, double* invd, double* red) {
-  const int P = blockDim.x;
-  const int tid = threadIdx.x;
-  int* ired = reinterpret_cast<int*>(red + 32);
-  for (int k = 0; k < n; ++k) {
-    // pivot search over column k, rows k..n-1 (NaN counts as +inf)
-    double best = -1.0;
-    int bi = n;
-    for (int i = k + tid; i < n; i += P) {
-      double v = fabs(A[(size_t)i * n + k]);
-      if (v != v) v = __longlong_as_double(0x7ff0000000000000LL);
-      if (v > best) { best = v; bi = i; }
-    }
+// LU with partial pivoting, register-tiled.  The CTA is a G x G grid of
+// threads; thread (tr, tc) holds the elements (tr + G r, tc + G c),
+// r, c < T, of the n x n row-major matrix A (shared memory, n <= G T) in
+// registers.  An FP64 instruction costs a full warp slot of the FP64 pipe
+// however few lanes are active, so every O(n)-per-step part avoids FP64:
+// pivot candidates are compared as integers (the bit pattern of |v| orders
+// like |v|, and NaN sorts above +inf), one thread forms the reciprocal pivot,
+// and one warp scales the multipliers.  Step k: the owners of column k
+// propose candidates, rows k and p are exchanged through shared memory, the
+// multipliers l_i = A_ik / A_kk and the pivot row u_j = A_kj are broadcast
+// through shared memory (lb, ub: n doubles each), and every thread applies
+// A_ij -= l_i u_j to its tile in registers.  On return A holds the unit lower
+// factor below the diagonal and the upper factor on and above it; piv[k] =
+// row exchanged with row k; invd[k] = 1 / U_kk.  Returns 0, or k+1 when pivot
+// k is zero or not finite (the same in every thread).  Ties pick the
+// smallest row index.  red: >= 3 G doubles of shared scratch.
+template <int G, int T>
+__device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, double* ub, double* red) {
+  const int tid = threadIdx.x, tr = tid / G, tc = tid - tr * G;
+  const unsigned long long ABS = 0x7fffffffffffffffULL, INFB = 0x7ff0000000000000ULL;
+  double a[T][T];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ov = __shfl_xor_sync(0xffffffffu, best, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ov > best || (ov == best && oi < bi)) { best = ov; bi = oi; }
+  for (int r = 0; r < T; ++r)
+#pragma unroll
+    for (int c = 0; c < T; ++c) {
+      const int i = tr + G * r, j = tc + G * c;
+      a[r][c] = (i < n && j < n) ? A[i * n + j] : 0.0;
     }
-    if (P > 32) {
-      __syncthreads();
-      if ((tid & 31) == 0) { red[tid >> 5] = best; ired[tid >> 5] = bi; }
-      __syncthreads();
-      best = red[0];
-      bi = ired[0];
-      for (int w = 1; w < (P >> 5); ++w)
-        if (red[w] > best || (red[w] == best && ired[w] < bi)) { best = red[w]; bi = ired[w]; }
+  unsigned long long* rk = reinterpret_cast<unsigned long long*>(red);  // [G] |candidate| bits
+  double* rs = red + G;                                                // [G] signed candidate
+  int* ri = reinterpret_cast<int*>(red + 2 * G);                       // [G] candidate row
+  int info = 0;
+  for (int k = 0; k < n; ++k) {
+    const int kq = k / G, kt = k - kq * G;
+    // 1. candidates from the owners of column k (tc == kt, slot kq)
+    if (tc == kt) {
+      unsigned long long best = 0;
+      double bsig = 0.0;
+      int bi = n;
+#pragma unroll
+      for (int c = 0; c < T; ++c) {
+        if (c != kq) continue;
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+          const int i = tr + G * r;
+          const unsigned long long key = (unsigned long long)__double_as_longlong(a[r][c]) & ABS;
+          if (i >= k && i < n && (bi == n || key > best)) {
+            best = key;
+            bsig = a[r][c];
+            bi = i;
+          }
+        }
+      }
+      rk[tr] = best;
+      rs[tr] = bsig;
+      ri[tr] = bi;
     }
-    if (!(best > 0.0) || !isfinite(best)) {
-      team_sync();
-      return k + 1;
-    }
-    if (tid == 0) piv[k] = bi;
-    if (bi != k) {
-      for (int j = tid; j < n; j += P) {
-        const double t = A[(size_t)k * n + j];
-        A[(size_t)k * n + j] = A[(size_t)bi * n + j];
-        A[(size_t)bi * n + j] = t;
+    __syncthreads();
+    unsigned long long best = 0;
+    double pv = 0.0;
+    int p = n;
+    for (int t = 0; t < G; ++t) {
+      if (ri[t] >= n) continue;
+      if (p == n || rk[t] > best || (rk[t] == best && ri[t] < p)) {
+        best = rk[t];
+        pv = rs[t];
+        p = ri[t];
       }
     }
-    team_sync();
-    const double ip = 1.0 / A[(size_t)k * n + k];
-    if (tid == 0) invd[k] = ip;
-    const int mrem = n - k - 1;
-    for (int i = k + 1 + tid; i < n; i += P) A[(size_t)i * n + k] *= ip;
-    team_sync();
-    // trailing update A[i][j] -= A[i][k] A[k][j], flattened over threads
-    const int cnt = mrem * mrem;
-    if (cnt > 0) {
-      int e = tid;
-      int ii = e / mrem, jj = e - ii * mrem;
-      const int di = P / mrem, dj = P - di * mrem;
-      for (; e < cnt; e += P) {
-        const int i = k + 1 + ii, j = k + 1 + jj;
-        A[(size_t)i * n + j] = fma(-A[(size_t)i * n + k], A[(size_t)k * n + j], A[(size_t)i * n + j]);
-        ii += di;
-        jj += dj;
-        if (jj >= mrem) { jj -= mrem; ++ii; }
+    if (p >= n || best == 0 || best >= INFB) {
+      info = k + 1;
+      break;
+    }
+    // 2. row interchange k <-> p
+    const int kt_r = k % G, ks_r = k / G, pt_r = p % G, ps_r = p / G;
+    if (p != k) {
+#pragma unroll
+      for (int r = 0; r < T; ++r) {
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+          const int j = tc + G * c;
+          if (j < n) {
+            if (tr == kt_r && r == ks_r) ub[j] = a[r][c];
+            if (tr == pt_r && r == ps_r) lb[j] = a[r][c];
+          }
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int r = 0; r < T; ++r) {
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+          const int j = tc + G * c;
+          if (j < n) {
+            if (tr == kt_r && r == ks_r) a[r][c] = lb[j];
+            if (tr == pt_r && r == ps_r) a[r][c] = ub[j];
+          }
+        }
+      }
+      __syncthreads();
+    }
+    // 3. unscaled column k below the diagonal, the pivot row, the reciprocal
+    if (tid == 0) {
+      piv[k] = p;
+      invd[k] = 1.0 / pv;
+    }
+    if (tc == kt) {
+#pragma unroll
+      for (int c = 0; c < T; ++c) {
+        if (c != kq) continue;
+#pragma unroll
+        for (int r = 0; r < T; ++r) {
+          const int i = tr + G * r;
+          if (i > k && i < n) lb[i] = a[r][c];
+        }
       }
     }
-    team_sync();
+    if (tr == kt_r) {
+#pragma unroll
+      for (int r = 0; r < T; ++r) {
+        if (r != ks_r) continue;
+#pragma unroll
+        for (int c = 0; c < T; ++c) {
+          const int j = tc + G * c;
+          if (j > k && j < n) ub[j] = a[r][c];
+        }
+      }
+    }
+    __syncthreads();
+    // one warp scales the multipliers
+    if (tid < 32) {
+      const double ip = invd[k];
+      for (int i = k + 1 + tid; i < n; i += 32) lb[i] *= ip;
+    }
+    __syncthreads();
+    // 4. multipliers into the L factor and rank-one update, in registers
+#pragma unroll
+    for (int r = 0; r < T; ++r) {
+      if (G * r + G - 1 <= k) continue;  // whole slot row above the block
+      const int i = tr + G * r;
+      const bool ri_ok = i > k && i < n;
+      const double li = ri_ok ? lb[i] : 0.0;
+#pragma unroll
+      for (int c = 0; c < T; ++c) {
+        if (G * c + G - 1 < k) continue;
+        const int j = tc + G * c;
+        if (ri_ok && j == k) a[r][c] = li;
+        if (ri_ok && j > k && j < n) a[r][c] = fma(-li, ub[j], a[r][c]);
+      }
+    }
   }
-  return 0;
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < T; ++r)
+#pragma unroll
+    for (int c = 0; c < T; ++c) {
+      const int i = tr + G * r, j = tc + G * c;
+      if (i < n && j < n) A[i * n + j] = a[r][c];
+    }
+  __syncthreads();
+  return info;
 }
 
-// Solve (LU) x = b in place (b in shared memory), pivots as from team_lu.
-__device__ void team_lu_solve(const double* A, int n, const int* piv, const double* invd, double* b) {
-  const int P = blockDim.x, tid = threadIdx.x;
-  if (tid == 0) {
+// Solve (LU) x = b in place with one warp (b in shared memory).  Must be
+// called by all 32 lanes of one warp; the caller orders it against the rest
+// of the CTA with a barrier.  Blocked by 32 rows: the dependence of a block on
+// earlier blocks is a matrix-vector product (one row per lane, four partial
+// sums in a fixed order), the diagonal block a substitution whose solved
+// value is broadcast by a shuffle.
+__device__ __forceinline__ void warp_lu_solve(const double* A, int n, const int* piv,
+                                              const double* invd, double* b) {
+  const int lane = threadIdx.x & 31;
+  if (lane == 0) {
     for (int k = 0; k < n; ++k) {
       const int p = piv[k];
-      if (p != k) { const double t = b[k]; b[k] = b[p]; b[p] = t; }
+      if (p != k) {
+        const double t = b[k];
+        b[k] = b[p];
+        b[p] = t;
+      }
     }
   }
-  team_sync();
-  // forward substitution with the unit lower triangle, column by column
-  for (int j = 0; j < n - 1; ++j) {
-    const double bj = b[j];
-    for (int i = j + 1 + tid; i < n; i += P) b[i] = fma(-A[(size_t)i * n + j], bj, b[i]);
-    team_sync();
+  __syncwarp();
+  // forward substitution with the unit lower triangle
+  for (int B0 = 0; B0 < n; B0 += 32) {
+    const int i = B0 + lane;
+    const bool act = i < n;
+    double s0 = act ? b[i] : 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (act) {
+      const double* Li = A + (size_t)i * n;
+      int j = 0;
+      for (; j + 4 <= B0; j += 4) {
+        s0 = fma(-Li[j], b[j], s0);
+        s1 = fma(-Li[j + 1], b[j + 1], s1);
+        s2 = fma(-Li[j + 2], b[j + 2], s2);
+        s3 = fma(-Li[j + 3], b[j + 3], s3);
+      }
+      for (; j < B0; ++j) s0 = fma(-Li[j], b[j], s0);
+    }
+    double s = (s0 + s1) + (s2 + s3);
+    const int m = min(32, n - B0);
+    for (int jj = 0; jj < m; ++jj) {
+      const double yj = __shfl_sync(0xffffffffu, s, jj);
+      if (act && lane > jj) s = fma(-A[(size_t)i * n + B0 + jj], yj, s);
+    }
+    if (act) b[i] = s;
+    __syncwarp();
   }
   // back substitution with U
-  for (int j = n - 1; j >= 0; --j) {
-    if (tid == 0) b[j] *= invd[j];
-    team_sync();
-    const double bj = b[j];
-    for (int i = tid; i < j; i += P) b[i] = fma(-A[(size_t)i * n + j], bj, b[i]);
-    team_sync();
+  for (int B1 = ((n - 1) / 32) * 32; B1 >= 0; B1 -= 32) {
+    const int i = B1 + lane;
+    const bool act = i < n;
+    const int m = min(32, n - B1);
+    double s0 = act ? b[i] : 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    if (act) {
+      const double* Ui = A + (size_t)i * n;
+      int j = B1 + 32;
+      for (; j + 4 <= n; j += 4) {
+        s0 = fma(-Ui[j], b[j], s0);
+        s1 = fma(-Ui[j + 1], b[j + 1], s1);
+        s2 = fma(-Ui[j + 2], b[j + 2], s2);
+        s3 = fma(-Ui[j + 3], b[j + 3], s3);
+      }
+      for (; j < n; ++j) s0 = fma(-Ui[j], b[j], s0);
+    }
+    double s = (s0 + s1) + (s2 + s3);
+    for (int jj = m - 1; jj >= 0; --jj) {
+      if (lane == jj) s *= invd[i];
+      const double xj = __shfl_sync(0xffffffffu, s, jj);
+      if (act && lane < jj) s = fma(-A[(size_t)i * n + B1 + jj], xj, s);
+    }
+    if (act) b[i] = s;
+    __syncwarp();
   }
 }
 

@@ -64,7 +64,7 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
     if (r.nreac > 2) fwd *= X[r.sp[2]];
     double net = kf * fwd;
     if (r.rev) {
-      double l2kc = (double)r.dnu * lp2;
+      double l2kc = r.dnu_d * lp2;
       l2kc += g2[r.sp[3]];
       if (r.nprod > 1) l2kc += g2[r.sp[4]];
       if (r.nprod > 2) l2kc += g2[r.sp[5]];
