@@ -119,8 +119,9 @@ typedef struct {
   double fixed_h;   /* > 0: constant step, no error control (order tests) */
   int32_t max_steps;/* attempted steps per reactor (accepted + rejected) */
   int32_t precision;/* 0: FP64 throughout */
-  int32_t variant;  /* 0: as many resident CTAs (ROS4) / blocks (RKF45) per SM as fit; > 0: cap per SM */
-  int32_t reserved;
+  int32_t variant;  /* 0: as many resident CTAs / blocks per SM as fit; > 0: cap per SM */
+  int32_t form;     /* RKF45 mapping: 0 automatic, 1 one thread per reactor (shallow),
+                       2 one CTA per reactor (deep); ROS4 always uses one CTA per reactor */
 } ck_solver_opts;
 
 /* Fills *opts with rtol 1e-9, atol 1e-12, h0 0, fixed_h 0, max_steps 100000. */

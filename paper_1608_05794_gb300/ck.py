@@ -49,11 +49,12 @@ class MechDesc(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h0", C.c_double), ("fixed_h", C.c_double),
                 ("max_steps", C.c_int32), ("precision", C.c_int32), ("variant", C.c_int32),
-                ("reserved", C.c_int32)]
+                ("form", C.c_int32)]
 
     @classmethod
-    def make(cls, rtol=1e-9, atol=1e-12, h0=0.0, fixed_h=0.0, max_steps=100000, precision=0, variant=0):
-        return cls(rtol, atol, h0, fixed_h, max_steps, precision, variant, 0)
+    def make(cls, rtol=1e-9, atol=1e-12, h0=0.0, fixed_h=0.0, max_steps=100000, precision=0, variant=0,
+             form=0):
+        return cls(rtol, atol, h0, fixed_h, max_steps, precision, variant, form)
 
 
 class WorkCounts(C.Structure):

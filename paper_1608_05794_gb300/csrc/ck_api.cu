@@ -559,6 +559,15 @@ int ck_lu_solve(int64_t batch, int32_t dim, const double* lu, const int32_t* piv
 
 namespace {
 
+// RKF45 mapping: explicit form, else one CTA per reactor unless the
+// mechanism is small (per-lane scratch stays on chip) and the batch fills
+// every SM with four 128-thread blocks of one reactor per thread.
+bool rkf45_team(const ck::HostMech& hm, int form, int64_t n) {
+  if (form == 1) return false;
+  if (form == 2) return true;
+  return hm.S > 32 || n < (int64_t)4 * 128 * ck::sm_count();
+}
+
 int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* y, const double* dt,
               double* h_io, const ck_solver_opts* opts, int32_t* steps, int32_t* status, void* stream) {
   if (!m) return fail(CK_EINVAL, "mech is NULL");
@@ -571,6 +580,7 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
   if (!(o.rtol > 0.0) || !(o.atol > 0.0) || o.max_steps < 1 || !(o.h0 >= 0.0) || !(o.fixed_h >= 0.0))
     return fail(CK_EINVAL, "opts: need rtol > 0, atol > 0, max_steps >= 1, h0 >= 0, fixed_h >= 0");
   if (o.precision != 0) return fail(CK_EINVAL, "opts.precision: only 0 (FP64) is available");
+  if (o.form < 0 || o.form > 2) return fail(CK_EINVAL, "opts.form must be 0, 1 or 2");
   if (int rc = check_device(m)) return rc;
   ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
   ck::LaunchCfg cfg;
@@ -603,6 +613,8 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
   if (e == cudaSuccess) {
     if (method == 0)
       e = ck::launch_ros4(m->hm, n, dp, dy, ddt, dh, sp, ds, dst, queue, st, cfg);
+    else if (rkf45_team(m->hm, o.form, n))
+      e = ck::launch_rkf45_team(m->hm, n, dp, dy, ddt, dh, sp, ds, dst, queue, st, cfg);
     else
       e = ck::launch_rkf45(m->hm, n, dp, dy, ddt, dh, sp, ds, dst, queue, st, cfg);
     cudaFreeAsync(queue, st);

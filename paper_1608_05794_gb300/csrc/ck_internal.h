@@ -53,6 +53,10 @@ cudaError_t launch_rkf45(const HostMech& hm, int64_t n, const double* p, double*
                          double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
                          int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);
 
+cudaError_t launch_rkf45_team(const HostMech& hm, int64_t n, const double* p, double* y,
+                              const double* dt, double* h_io, const SolverParams& sp, int32_t* steps,
+                              int32_t* status, int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);
+
 int sm_count();
 
 // Allocation-free ROS4 (ck_integrate_ros4_noalloc): the work-queue counter

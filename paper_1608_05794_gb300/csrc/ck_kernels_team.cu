@@ -312,6 +312,149 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64
   }
 }
 
+// ------------------------------------------------------------------ RKF45 (team)
+// RKF45 with one CTA per reactor (the paper's "deep" form): the six stage
+// right-hand sides are evaluated by the team, so a reactor's working set
+// (8 n-vectors and one chunk of reaction scratch) stays in shared memory and
+// the number of steps of one reactor never holds back another.
+__global__ void __launch_bounds__(64) k_rkf45_team(DevMech d, int64_t N, const double* __restrict__ p,
+                                                   double* __restrict__ y, const double* __restrict__ dt,
+                                                   double* h_io, SolverParams sp, int32_t* steps,
+                                                   int32_t* status, int32_t* queue) {
+  extern __shared__ __align__(16) double sm[];
+  __shared__ int slot;
+  const int n = d.n;
+  double* yv = sm;
+  double* yt = yv + n;
+  double* kk = yt + n;  // six stages, n each
+  TeamBufs b = carve_bufs(kk + 6 * n, d.S, d.chunk);
+  Mix x;
+  const bool fixed = sp.fixed_h > 0.0;
+  const int tid = threadIdx.x, P = blockDim.x;
+  double* k0 = kk;
+  double* k1 = kk + n;
+  double* k2 = kk + 2 * n;
+  double* k3 = kk + 3 * n;
+  double* k4 = kk + 4 * n;
+  double* k5 = kk + 5 * n;
+  for (;;) {
+    const int r = team_next(queue, &slot);
+    if (r >= N) break;
+    for (int i = tid; i < n; i += P) yv[i] = y[(int64_t)r * n + i];
+    const double pr = p[r];
+    const double tf = dt[r];
+    __syncthreads();
+    int bad = 0;
+    for (int i = tid; i < n; i += P) bad |= !isfinite(yv[i]);
+    bad = __syncthreads_or(bad);
+    bad |= !(pr > 0.0) || !isfinite(pr) || !(yv[0] > 0.0) || !isfinite(tf) || !(tf >= 0.0);
+    int st = ST_OK, acc = 0, rej = 0;
+    double h = 0.0;
+    if (bad) {
+      st = ST_BADINPUT;
+    } else if (tf > 0.0) {
+      if (fixed) h = sp.fixed_h;
+      else if (h_io && h_io[r] > 0.0) h = h_io[r];
+      else if (sp.h0 > 0.0) h = sp.h0;
+      else h = team_h0(d, d.tab, pr, yv, tf, sp.rtol, sp.atol, k0, yt, k1, b, x);
+      const double hmin = 1e-15 * tf;
+      double t = 0.0;
+      bool last_rej = false, last_nf = false;
+      while (t < tf) {
+        if (acc + rej >= sp.max_steps) { st = ST_MAXSTEPS; break; }
+        const bool clamped = h >= tf - t;
+        const double hh = clamped ? tf - t : h;
+        if (hh < hmin) { st = last_nf ? ST_NONFINITE : ST_HMIN; break; }
+        // k_s = hh f(y + sum_j a_sj k_j)
+        team_rhs(d, d.tab, pr, yv, k0, b, x);
+        for (int i = tid; i < n; i += P) {
+          k0[i] *= hh;
+          yt[i] = fma(RK_A21, k0[i], yv[i]);
+        }
+        team_sync();
+        team_rhs(d, d.tab, pr, yt, k1, b, x);
+        for (int i = tid; i < n; i += P) {
+          k1[i] *= hh;
+          yt[i] = fma(RK_A32, k1[i], fma(RK_A31, k0[i], yv[i]));
+        }
+        team_sync();
+        team_rhs(d, d.tab, pr, yt, k2, b, x);
+        for (int i = tid; i < n; i += P) {
+          k2[i] *= hh;
+          yt[i] = fma(RK_A43, k2[i], fma(RK_A42, k1[i], fma(RK_A41, k0[i], yv[i])));
+        }
+        team_sync();
+        team_rhs(d, d.tab, pr, yt, k3, b, x);
+        for (int i = tid; i < n; i += P) {
+          k3[i] *= hh;
+          yt[i] = fma(RK_A54, k3[i], fma(RK_A53, k2[i], fma(RK_A52, k1[i], fma(RK_A51, k0[i], yv[i]))));
+        }
+        team_sync();
+        team_rhs(d, d.tab, pr, yt, k4, b, x);
+        for (int i = tid; i < n; i += P) {
+          k4[i] *= hh;
+          yt[i] = fma(RK_A65, k4[i],
+                      fma(RK_A64, k3[i], fma(RK_A63, k2[i], fma(RK_A62, k1[i], fma(RK_A61, k0[i], yv[i])))));
+        }
+        team_sync();
+        team_rhs(d, d.tab, pr, yt, k5, b, x);
+        // y* = y + sum b k (into yt), e = sum (bh - b) k (into k1, whose weights are 0)
+        int nf = 0;
+        for (int i = tid; i < n; i += P) {
+          k5[i] *= hh;
+          const double yn =
+              fma(RK_B5, k4[i], fma(RK_B4, k3[i], fma(RK_B3, k2[i], fma(RK_B1, k0[i], yv[i]))));
+          k1[i] = fma(RK_D6, k5[i], fma(RK_D5, k4[i], fma(RK_D4, k3[i], fma(RK_D3, k2[i], RK_D1 * k0[i]))));
+          yt[i] = yn;
+          nf |= !isfinite(yn);
+        }
+        nf = __syncthreads_or(nf);
+        if (fixed) {
+          for (int i = tid; i < n; i += P) yv[i] = yt[i];
+          team_sync();
+          t = clamped ? tf : t + hh;
+          ++acc;
+          continue;
+        }
+        const double e = team_wrms(n, k1, yv, yt, sp.rtol, sp.atol, b.red);
+        if (nf || !isfinite(e)) {
+          ++rej;
+          h = FAC_MIN * hh;
+          last_rej = true;
+          last_nf = true;
+          continue;
+        }
+        last_nf = false;
+        if (e < 1.0) {
+          for (int i = tid; i < n; i += P) yv[i] = yt[i];
+          team_sync();
+          t = clamped ? tf : t + hh;
+          ++acc;
+          double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(e, -0.2)));
+          if (last_rej) fac = fmin(1.0, fac);
+          h = hh * fac;
+          last_rej = false;
+        } else {
+          ++rej;
+          h = hh * fmax(FAC_MIN, SAFETY * pow(e, -0.2));
+          last_rej = true;
+        }
+      }
+    }
+    __syncthreads();
+    for (int i = tid; i < n; i += P) y[(int64_t)r * n + i] = yv[i];
+    if (tid == 0) {
+      if (h_io && st != ST_BADINPUT && tf > 0.0) h_io[r] = h;
+      if (steps) {
+        steps[2 * (int64_t)r] = acc;
+        steps[2 * (int64_t)r + 1] = rej;
+      }
+      status[r] = st;
+    }
+    __syncthreads();
+  }
+}
+
 // ------------------------------------------------------------------ launchers
 static int team_threads(int n, const LaunchCfg& cfg) {
   int w = cfg.team_warps;
@@ -397,6 +540,19 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
     kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
     return cudaGetLastError();
   });
+}
+
+cudaError_t launch_rkf45_team(const HostMech& hm, int64_t n, const double* p, double* y,
+                              const double* dt, double* h_io, const SolverParams& sp, int32_t* steps,
+                              int32_t* status, int32_t* queue, cudaStream_t st, const LaunchCfg& cfg) {
+  if (n <= 0) return cudaSuccess;
+  const int nn = hm.d.n;
+  const size_t smem = sizeof(double) * (8 * (size_t)nn + team_bufs_doubles(hm.S, hm.d.chunk));
+  const int grid = team_grid(k_rkf45_team, 64, smem, n, cfg);
+  cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
+  if (e != cudaSuccess) return e;
+  k_rkf45_team<<<grid, 64, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
+  return cudaGetLastError();
 }
 
 // ------------------------------------------------------------------ allocation-free ROS4

@@ -196,7 +196,7 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
 }
 
 // f(y) for one reactor.  y, f: shared memory, n = S + 1.
-static __device__ void team_rhs(const DevMech& m, const double* tab, double p, const double* y, double* f,
+static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab, double p, const double* y, double* f,
                          TeamBufs& b, Mix& x) {
   team_species(m, p, y, b, x, false);
   team_sync();

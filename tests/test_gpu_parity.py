@@ -152,13 +152,16 @@ def _assert_states_close(y, yo, st, sto):
     assert dY.max() <= ATOL_STATE_Y, dY.max()
 
 
-@pytest.mark.parametrize("method", [ORA_ROS4, ORA_RKF45])
-def test_integrate_small_config_full(ck, method):
+FORMS = [(ORA_ROS4, 0), (ORA_RKF45, 1), (ORA_RKF45, 2)]
+
+
+@pytest.mark.parametrize("method,form", FORMS)
+def test_integrate_small_config_full(ck, method, form):
     name = "small"
     m, gm, om = _mech(ck, name)
     cfg = CONFIGS[name]
     y, p = reactor_states(name)
-    yg, sg, stg, hg = _integrate_gpu(ck, gm, method, p, y, cfg["dt"])
+    yg, sg, stg, hg = _integrate_gpu(ck, gm, method, p, y, cfg["dt"], form=form)
     yo, so, sto, ho = om.integrate(method, p, y, cfg["dt"], h_inout=np.zeros(len(p)))
     _assert_states_close(yg, yo, stg, sto)
     assert np.all(stg == 0)
@@ -166,13 +169,13 @@ def test_integrate_small_config_full(ck, method):
     assert np.abs(sg.sum(1) - so.sum(1)).max() <= 0.1 * so.sum(1).max() + 3
 
 
-@pytest.mark.parametrize("method", [ORA_ROS4, ORA_RKF45])
+@pytest.mark.parametrize("method,form", FORMS)
 @pytest.mark.parametrize("name,n", [("medium", 48), ("large", 12)])
-def test_integrate_sampled(ck, method, name, n):
+def test_integrate_sampled(ck, method, form, name, n):
     m, gm, om = _mech(ck, name)
     cfg = CONFIGS[name]
     y, p = reactor_states(name, n=n, seed_offset=5)
-    yg, sg, stg, _ = _integrate_gpu(ck, gm, method, p, y, cfg["dt"])
+    yg, sg, stg, _ = _integrate_gpu(ck, gm, method, p, y, cfg["dt"], form=form)
     yo, so, sto, _ = om.integrate(method, p, y, cfg["dt"])
     _assert_states_close(yg, yo, stg, sto)
 
@@ -199,8 +202,8 @@ def test_edge_cases(ck):
     dt = np.array([1e-5, 1e-5, 1e-5, 0.0, 1e-5])
     p = p.copy()
     p[4] = 0.0            # p <= 0
-    for method in (ORA_ROS4, ORA_RKF45):
-        yg, sg, stg, _ = _integrate_gpu(ck, gm, method, p, y, dt)
+    for method, form in FORMS:
+        yg, sg, stg, _ = _integrate_gpu(ck, gm, method, p, y, dt, form=form)
         assert stg.tolist() == [0, 5, 5, 0, 5]
         assert sg[3].tolist() == [0, 0] and np.array_equal(yg[3], y[3])
     # max_steps
