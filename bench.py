@@ -336,6 +336,88 @@ def run_ours(args):
         torch.distributed.destroy_process_group()
 
 
+def run_serve(args):
+    """Serving trace: Poisson arrivals of reactor batches (log-uniform
+    1k-256k cells, one of the three mechanisms, dt log-uniform 1e-6..1e-4 s,
+    ROS4 in the precision form or RKF45 50/50), state resident on the device.
+    Latency = completion - arrival.  The continuous-batching server is
+    compared with the plain form: one synchronous integration per request,
+    first come first served."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from synth.configs import CONFIGS, load_mechanism, reactor_states
+    names = ["small", "medium", "large"]
+    mechs = {nm: ck.load_mechanism(load_mechanism(CONFIGS[nm]["mech"])) for nm in names}
+    rng = np.random.default_rng(2004)
+    K = args.requests
+    arrivals = np.cumsum(rng.exponential(1.0 / args.rate, K))
+    reqs = []
+    for i in range(K):
+        nm = names[int(rng.integers(3))]
+        cells = int(round(10 ** rng.uniform(3, np.log10(256e3))))
+        dt = 10 ** rng.uniform(-6, -4)
+        method = int(rng.integers(2))
+        y, p = reactor_states(nm, n=cells, seed_offset=500 + i)
+        reqs.append(dict(name=nm, n=cells, dt=dt, method=method, y=torch.as_tensor(y, device="cuda"),
+                         p=torch.as_tensor(p, device="cuda")))
+    def opts_for(r):
+        return ck.SolverOpts.make(precision=1 if r["method"] == 0 else 0)
+
+    def fresh(r):
+        return (r["y"].clone(), torch.full((r["n"],), r["dt"], dtype=torch.float64, device="cuda"),
+                torch.empty(r["n"], dtype=torch.int32, device="cuda"))
+
+    out = {}
+    for form in ("server", "plain"):
+        bufs = [fresh(r) for r in reqs]
+        torch.cuda.synchronize()
+        lat = [0.0] * K
+        t0 = time.perf_counter()
+        if form == "server":
+            srv = ck.Server(hbm_budget_bytes=args.budget_gb << 30, streams=args.streams, chunk_reactors=args.chunk)
+            tickets = {}
+            pending = set()
+            i = 0
+            while i < K or pending:
+                now = time.perf_counter() - t0
+                while i < K and arrivals[i] <= now:
+                    y, dt, st = bufs[i]
+                    tickets[i] = srv.submit(mechs[reqs[i]["name"]], reqs[i]["method"], reqs[i]["p"], y, dt, st,
+                                            opts=opts_for(reqs[i]))
+                    pending.add(i)
+                    i += 1
+                for j in list(pending):
+                    if srv.poll(tickets[j]) != 0:
+                        lat[j] = time.perf_counter() - t0 - arrivals[j]
+                        pending.discard(j)
+                time.sleep(0.0005)
+            srv.close()
+        else:
+            for i in range(K):
+                now = time.perf_counter() - t0
+                if arrivals[i] > now:
+                    time.sleep(arrivals[i] - now)
+                y, dt, st = bufs[i]
+                fn = ck.integrate_ros4 if reqs[i]["method"] == 0 else ck.integrate_rkf45
+                fn(mechs[reqs[i]["name"]], reqs[i]["p"], y, dt, st, opts=opts_for(reqs[i]))
+                torch.cuda.synchronize()
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+        makespan = time.perf_counter() - t0
+        ok = all(bool((b[2] == 0).all().item()) for b in bufs)
+        cells = sum(r["n"] for r in reqs)
+        out[form] = {"p50_ms": 1e3 * float(np.percentile(lat, 50)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+                     "reactors_per_s": cells / makespan, "makespan_s": makespan, "all_ok": ok}
+    line = {"mode": "serve", "metric": METRIC, "requests": K, "rate_per_s": args.rate,
+            "cells_total": int(sum(r["n"] for r in reqs)),
+            "trace": "seed 2004: Poisson arrivals; cells log-uniform 1e3-2.56e5; mechanism uniform over the "
+                     "10/53/111-species stand-ins; dt log-uniform 1e-6-1e-4 s; ROS4 (precision 1) or RKF45 "
+                     "50/50; state resident on the device",
+            "server": out["server"], "plain": out["plain"],
+            "server_config": {"budget_gb": args.budget_gb, "streams": args.streams, "chunk_reactors": args.chunk}}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(args):
     """A small case of one kernel for ncu (warm-up launches, then 3 launches)."""
     import torch
@@ -377,8 +459,16 @@ def main():
                     help="profiling only: launch one kernel a few times on a small batch, print no bench line")
     ap.add_argument("--reactors", type=int, default=2048, help="batch size of --profile-case")
     ap.add_argument("--dt", type=float, default=None, help="dt of --profile-case (default: the workload's)")
+    ap.add_argument("--mode", choices=["bench", "serve"], default="bench")
+    ap.add_argument("--requests", type=int, default=12, help="serve: requests in the trace")
+    ap.add_argument("--rate", type=float, default=500.0, help="serve: Poisson arrival rate, requests/s")
+    ap.add_argument("--budget-gb", type=int, default=64, help="serve: HBM budget of the server")
+    ap.add_argument("--streams", type=int, default=4, help="serve: server streams")
+    ap.add_argument("--chunk", type=int, default=8192, help="serve: reactors per launched chunk")
     args = ap.parse_args()
-    if args.profile_case:
+    if args.mode == "serve":
+        run_serve(args)
+    elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -118,7 +118,10 @@ typedef struct {
   double h0;        /* > 0: first step size; 0: estimate */
   double fixed_h;   /* > 0: constant step, no error control (order tests) */
   int32_t max_steps;/* attempted steps per reactor (accepted + rejected) */
-  int32_t precision;/* 0: FP64 throughout */
+  int32_t precision;/* 0: FP64 throughout; 1 or 2 (ROS4): the LU factor and stage solves in FP32,
+                       each solve refined once or twice against the FP64 iteration matrix; the
+                       rates, K_c, the temperature equation, the error norm and step control
+                       stay FP64 */
   int32_t variant;  /* 0: as many resident CTAs / blocks per SM as fit; > 0: cap per SM */
   int32_t form;     /* RKF45 mapping: 0 automatic, 1 one thread per reactor (shallow),
                        2 one CTA per reactor (deep); ROS4 always uses one CTA per reactor */
@@ -179,6 +182,47 @@ int ck_integrate_ros4(const ck_mech* mech, int64_t n, const double* p, double* y
 int ck_integrate_rkf45(const ck_mech* mech, int64_t n, const double* p, double* y, const double* dt,
                        double* h_inout, const ck_solver_opts* opts, int32_t* steps, int32_t* status,
                        void* stream);
+
+/* ---------------------------------------------------------------- serving
+ * A request server for reactor batches that arrive over time (continuous
+ * batching; no counterpart in the paper, which integrates one fixed batch).
+ * A request is admitted, in arrival order, once its device footprint
+ * (n * ((S+1)*8 + 28) bytes: state, p, dt, status, step counts) fits the
+ * HBM budget; admitted requests are split into chunks of chunk_reactors
+ * reactors that a dispatcher thread launches round-robin on `streams` CUDA
+ * streams, so work that arrives while other requests run starts at once and
+ * overlaps them on the device.  A request's arrays are all host memory
+ * (staged by the server; pin them for asynchronous copies) or all device
+ * memory (used in place), and must stay valid until the request is done.
+ * Each reactor is integrated independently, so results do not depend on the
+ * other requests in flight. */
+typedef struct ck_server ck_server;
+typedef struct {
+  int64_t queued, active, completed;
+  uint64_t bytes_in_use, budget;
+} ck_server_info;
+/* Create a server on the current device.  streams in [1, 64];
+ * chunk_reactors <= 0 selects 8192. */
+int ck_server_create(size_t hbm_budget_bytes, int32_t streams, int64_t chunk_reactors, ck_server** out);
+/* Queue a request: method 0 ROS4, 1 RKF45; the same arrays and options as
+ * ck_integrate_*; steps may be NULL.  *ticket identifies it.  CK_AGAIN if
+ * the request alone exceeds the budget. */
+int ck_submit(ck_server* srv, const ck_mech* mech, int32_t method, int64_t n, const double* p, double* y,
+              const double* dt, const ck_solver_opts* opts, int32_t* status, int32_t* steps,
+              uint64_t* ticket);
+/* Non-blocking state: *state = 0 in flight, 1 done, 2 failed (the call
+ * returns the failure code), 3 cancelled. */
+int ck_poll(ck_server* srv, uint64_t ticket, int32_t* state);
+/* Block until the request is done, failed or cancelled, or timeout_s
+ * elapses (CK_TIMEOUT). */
+int ck_wait(ck_server* srv, uint64_t ticket, double timeout_s);
+/* Cancel a request that has not been admitted yet (CK_AGAIN otherwise). */
+int ck_cancel(ck_server* srv, uint64_t ticket);
+/* Forget a finished request (CK_AGAIN while in flight). */
+int ck_release(ck_server* srv, uint64_t ticket);
+int ck_server_stats(ck_server* srv, ck_server_info* out);
+/* Stop the dispatcher, wait for the device, free everything. */
+int ck_server_destroy(ck_server* srv);
 
 /* Allocation-free variant of ck_integrate_ros4 (no counterpart in the paper).
  * Same arguments, arithmetic and results as ck_integrate_ros4, for callers

@@ -18,7 +18,7 @@ from .build import LIB, build
 
 __all__ = [
     "Mechanism", "load_mechanism", "rhs", "jacobian", "lu_factor", "lu_solve", "integrate_ros4",
-    "integrate_rkf45", "integrate_ros4_noalloc", "count_work", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
+    "integrate_rkf45", "integrate_ros4_noalloc", "count_work", "Server", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
 ]
 
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "HMIN", 3: "NONFINITE", 4: "SINGULAR", 5: "BADINPUT"}
@@ -63,6 +63,11 @@ class WorkCounts(C.Structure):
                                            "integrate_bytes")]
 
 
+class ServerInfo(C.Structure):
+    _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
+                ("bytes_in_use", C.c_uint64), ("budget", C.c_uint64)]
+
+
 def _bind():
     L = _lib
     L.ck_load_mechanism.argtypes = [C.POINTER(MechDesc), C.POINTER(C.c_void_p)]
@@ -77,6 +82,15 @@ def _bind():
     L.ck_integrate_ros4_noalloc.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, _DP, C.POINTER(SolverOpts), _DP,
                                             _DP, _DP]
     L.ck_count_work.argtypes = [C.c_void_p, C.POINTER(WorkCounts)]
+    L.ck_server_create.argtypes = [C.c_size_t, C.c_int32, C.c_int64, C.POINTER(C.c_void_p)]
+    L.ck_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, _DP, _DP, _DP, C.POINTER(SolverOpts),
+                            _DP, _DP, C.POINTER(C.c_uint64)]
+    L.ck_poll.argtypes = [C.c_void_p, C.c_uint64, C.POINTER(C.c_int32)]
+    L.ck_wait.argtypes = [C.c_void_p, C.c_uint64, C.c_double]
+    L.ck_cancel.argtypes = [C.c_void_p, C.c_uint64]
+    L.ck_release.argtypes = [C.c_void_p, C.c_uint64]
+    L.ck_server_stats.argtypes = [C.c_void_p, C.POINTER(ServerInfo)]
+    L.ck_server_destroy.argtypes = [C.c_void_p]
     L.ck_device_errors.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]
     L.ck_status_str.restype = C.c_char_p
     L.ck_last_error.restype = C.c_char_p
@@ -236,6 +250,60 @@ def integrate_ros4_noalloc(mech, p, y, dt, status, h_inout=None, steps=None, opt
     tensors only; calls on one device must not overlap on the GPU."""
     _integrate(_lib.ck_integrate_ros4_noalloc, "ck_integrate_ros4_noalloc", mech, p, y, dt, status, h_inout,
                steps, opts, stream)
+
+
+class Server:
+    """Request server with continuous batching (ck_server_*).  Arrays passed
+    to submit() must stay alive until the request is done."""
+
+    ROS4, RKF45 = 0, 1
+
+    def __init__(self, hbm_budget_bytes: int, streams: int = 4, chunk_reactors: int = 0):
+        h = C.c_void_p()
+        _check(_lib.ck_server_create(int(hbm_budget_bytes), int(streams), int(chunk_reactors), C.byref(h)),
+               "ck_server_create")
+        self.h = h
+        self._keep = {}
+
+    def submit(self, mech, method, p, y, dt, status, steps=None, opts=None) -> int:
+        t = C.c_uint64()
+        o = opts if opts is not None else SolverOpts.make()
+        _check(_lib.ck_submit(self.h, mech.h, int(method), y.shape[0], _ptr(p), _ptr(y), _ptr(dt), C.byref(o),
+                              _ptr(status), _ptr(steps), C.byref(t)), "ck_submit")
+        self._keep[t.value] = (p, y, dt, status, steps, o)
+        return t.value
+
+    def poll(self, ticket) -> int:
+        st = C.c_int32()
+        _check(_lib.ck_poll(self.h, int(ticket), C.byref(st)), "ck_poll")
+        return st.value
+
+    def wait(self, ticket, timeout_s=600.0):
+        _check(_lib.ck_wait(self.h, int(ticket), float(timeout_s)), "ck_wait")
+
+    def cancel(self, ticket):
+        _check(_lib.ck_cancel(self.h, int(ticket)), "ck_cancel")
+
+    def release(self, ticket):
+        _check(_lib.ck_release(self.h, int(ticket)), "ck_release")
+        self._keep.pop(int(ticket), None)
+
+    def stats(self) -> dict:
+        i = ServerInfo()
+        _check(_lib.ck_server_stats(self.h, C.byref(i)), "ck_server_stats")
+        return {k: getattr(i, k) for k, _ in ServerInfo._fields_}
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ck_server_destroy(self.h)
+            self.h = None
+            self._keep.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def count_work(mech: Mechanism) -> dict:

@@ -13,10 +13,6 @@
 #include "../../include/ck.h"
 #include "ck_internal.h"
 
-struct ck_mech {
-  ck::HostMech hm;
-};
-
 namespace {
 
 thread_local std::string g_err;
@@ -172,6 +168,8 @@ int validate(const ck_mech_desc* d) {
 }
 
 }  // namespace
+
+int ck::set_error(int code, const char* msg) { return fail(code, msg); }
 
 extern "C" {
 
@@ -579,12 +577,15 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
   else ck_default_opts(&o);
   if (!(o.rtol > 0.0) || !(o.atol > 0.0) || o.max_steps < 1 || !(o.h0 >= 0.0) || !(o.fixed_h >= 0.0))
     return fail(CK_EINVAL, "opts: need rtol > 0, atol > 0, max_steps >= 1, h0 >= 0, fixed_h >= 0");
-  if (o.precision != 0) return fail(CK_EINVAL, "opts.precision: only 0 (FP64) is available");
+  if (o.precision < 0 || o.precision > 2 || (o.precision != 0 && method != 0))
+    return fail(CK_EINVAL, "opts.precision: 0 (FP64) for both methods; 1 or 2 (FP32 LU + 1 or 2 FP64 "
+                           "refinement steps) for ROS4");
   if (o.form < 0 || o.form > 2) return fail(CK_EINVAL, "opts.form must be 0, 1 or 2");
   if (int rc = check_device(m)) return rc;
   ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
   ck::LaunchCfg cfg;
   if (o.variant > 0) cfg.ctas_per_sm = o.variant;
+  cfg.precision = o.precision;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = (size_t)m->hm.d.n;
   const bool host = is_host_ptr(p) || is_host_ptr(y) || is_host_ptr(dt) || is_host_ptr(h_io) ||

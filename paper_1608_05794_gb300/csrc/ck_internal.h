@@ -36,6 +36,7 @@ enum : int32_t { DEVERR_STAGE_TIMEOUT = 1 };
 struct LaunchCfg {
   int team_warps = 0;   // warps per reactor for team kernels (0: heuristic)
   int ctas_per_sm = 0;  // 0: as many as fit
+  int precision = 0;    // ROS4 linear algebra: 0 FP64, 1 FP32 + FP64 refinement
 };
 
 cudaError_t launch_rhs(const HostMech& hm, int64_t n, const double* p, const double* y, double* f,
@@ -59,6 +60,9 @@ cudaError_t launch_rkf45_team(const HostMech& hm, int64_t n, const double* p, do
 
 int sm_count();
 
+// Record a failure message for ck_last_error() and return code.
+int set_error(int code, const char* msg);
+
 // Allocation-free ROS4 (ck_integrate_ros4_noalloc): the work-queue counter
 // lives in a static device array of NOALLOC_SCRATCH_INTS ints.
 constexpr int NOALLOC_SCRATCH_INTS = 64;
@@ -70,3 +74,8 @@ cudaError_t launch_ros4_noalloc(const HostMech& hm, int64_t n, const double* p, 
                                 const LaunchCfg& cfg);
 
 }  // namespace ck
+
+// Library-owned handle of a loaded mechanism (opaque in the C ABI).
+struct ck_mech {
+  ck::HostMech hm;
+};

@@ -13,7 +13,7 @@
 
 namespace ck {
 
-__host__ __device__ __forceinline__ int team_bufs_doubles(int S, int chunk) { return 9 * S + (3 + JP) * chunk + 32; }
+__host__ __device__ __forceinline__ int team_bufs_doubles(int S, int chunk) { return 9 * S + (3 + JP) * chunk + 48; }
 
 __device__ __forceinline__ TeamBufs carve_bufs(double* base, int S, int CH) {
   TeamBufs b;
@@ -45,7 +45,7 @@ __device__ __forceinline__ int team_next(int32_t* queue, int* slot) {
 }
 
 // ------------------------------------------------------------------ Jacobian
-__global__ void k_jacobian(DevMech d, int64_t N, const double* __restrict__ p,
+__global__ void k_jacobian(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
                            const double* __restrict__ y, double* __restrict__ jac) {
   extern __shared__ __align__(16) double sm[];
   const int n = d.n;
@@ -131,7 +131,7 @@ __device__ double team_h0(const DevMech& d, const double* tab, double p, const d
                           double rtol, double atol, double* f0, double* y1, double* f1, TeamBufs& b,
                           Mix& x) {
   const int n = d.n;
-  team_rhs(d, tab, p, y0, f0, b, x);
+  team_rhs(d, tab, p, y0, f0, b);
   double s0 = 0.0, s1 = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double sc = atol + rtol * fabs(y0[i]);
@@ -143,7 +143,7 @@ __device__ double team_h0(const DevMech& d, const double* tab, double p, const d
   const double ha = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
   for (int i = threadIdx.x; i < n; i += blockDim.x) y1[i] = fma(ha, f0[i], y0[i]);
   team_sync();
-  team_rhs(d, tab, p, y1, f1, b, x);
+  team_rhs(d, tab, p, y1, f1, b);
   double s2 = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double sc = atol + rtol * fabs(y0[i]);
@@ -156,8 +156,50 @@ __device__ double team_h0(const DevMech& d, const double* tab, double p, const d
   return fmin(fmin(100.0 * ha, hb), tspan);
 }
 
-template <int G, int T>
-__global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64_t N, const double* __restrict__ p,
+// Stage solve of the precision form: the iteration matrix is factored in
+// FP32 (M32, piv, invd32) and each solve is refined against the FP64 matrix
+// M64: x = LU32^-1 b, then REFINE times r = b - M64 x (FP64), x += LU32^-1 r.
+// b (in u) is overwritten with x; xf (n floats) and x (n doubles) are scratch
+// that must not hold anything the caller still needs (stage 4 reuses the
+// third stage's f, so the first three solves take u4's buffer as xf).
+__device__ void refined_solve(const double* M64, const float* M32, int n, const int* piv,
+                              const float* invd32, double* u, float* xf, double* x, int refine) {
+  const int tid = threadIdx.x, P = blockDim.x;
+  for (int i = tid; i < n; i += P) xf[i] = (float)u[i];
+  __syncthreads();
+  if (tid < 32) warp_lu_solve(M32, n, piv, invd32, xf);
+  __syncthreads();
+  for (int i = tid; i < n; i += P) x[i] = (double)xf[i];
+  __syncthreads();
+  for (int it = 0; it < refine; ++it) {
+    for (int i = tid; i < n; i += P) {
+      const double* row = M64 + (size_t)i * n;
+      double s0 = u[i], s1 = 0.0, s2 = 0.0, s3 = 0.0;
+      int j = 0;
+      for (; j + 4 <= n; j += 4) {
+        s0 = fma(-row[j], x[j], s0);
+        s1 = fma(-row[j + 1], x[j + 1], s1);
+        s2 = fma(-row[j + 2], x[j + 2], s2);
+        s3 = fma(-row[j + 3], x[j + 3], s3);
+      }
+      for (; j < n; ++j) s0 = fma(-row[j], x[j], s0);
+      xf[i] = (float)((s0 + s1) + (s2 + s3));
+    }
+    __syncthreads();
+    if (tid < 32) warp_lu_solve(M32, n, piv, invd32, xf);
+    __syncthreads();
+    for (int i = tid; i < n; i += P) x[i] += (double)xf[i];
+    __syncthreads();
+  }
+  for (int i = tid; i < n; i += P) u[i] = x[i];
+  __syncthreads();
+}
+
+// PREC 0: FP64 LU and solves.  PREC 1 / 2: FP32 LU and solves with one /
+// two steps of FP64 iterative refinement (the rates, K_c, the temperature
+// equation, the error norm and the step control stay FP64).
+template <int G, int T, int PREC>
+__global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
                                                  double* __restrict__ y, const double* __restrict__ dt,
                                                  double* h_io, SolverParams sp, int32_t* steps,
                                                  int32_t* status, int32_t* queue) {
@@ -179,6 +221,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64
   double* lb = F;   // LU broadcast buffers: F and Yt are free while factoring
   double* ub = Yt;
   TeamBufs b = carve_bufs(invd + n + (n + 1) / 2, d.S, d.chunk);
+  float* M32 = reinterpret_cast<float*>(b.red + 48);  // PREC >= 1 only: n x n floats
   Mix x;
   const bool fixed = sp.fixed_h > 0.0;
   const int tid = threadIdx.x, P = blockDim.x;
@@ -218,7 +261,15 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64
         team_sync();
         for (int i = tid; i < n; i += P) M[(size_t)i * n + i] += dg;
         team_sync();
-        const int info = lu_reg<G, T>(M, n, piv, invd, lb, ub, b.red);
+        int info;
+        if (PREC == 0) {
+          info = lu_reg<G, T>(M, n, piv, invd, lb, ub, b.red);
+        } else {
+          for (int e = tid; e < n * n; e += P) M32[e] = (float)M[e];
+          __syncthreads();
+          info = lu_reg<G, T>(M32, n, piv, reinterpret_cast<float*>(invd), reinterpret_cast<float*>(lb),
+                              reinterpret_cast<float*>(ub), b.red);
+        }
         if (info) {
           ++rej;
           if (++sing_run >= SINGULAR_LIMIT) { st = ST_SINGULAR; break; }
@@ -231,31 +282,47 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64
         // stage 1: M u1 = f(y)
         for (int i = tid; i < n; i += P) u1[i] = F0[i];
         team_sync();
-        if (tid < 32) warp_lu_solve(M, n, piv, invd, u1);
-        __syncthreads();
+        if (PREC == 0) {
+          if (tid < 32) warp_lu_solve(M, n, piv, invd, u1);
+          __syncthreads();
+        } else {
+          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u1, reinterpret_cast<float*>(u4), Yt, PREC);
+        }
         // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
         for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A21, u1[i], yv[i]);
         team_sync();
-        team_rhs(d, tab, pr, Yt, F, b, x);
+        team_rhs(d, tab, pr, Yt, F, b);
         for (int i = tid; i < n; i += P) u2[i] = fma(ROS_C21 * ih, u1[i], F[i]);
         team_sync();
-        if (tid < 32) warp_lu_solve(M, n, piv, invd, u2);
-        __syncthreads();
+        if (PREC == 0) {
+          if (tid < 32) warp_lu_solve(M, n, piv, invd, u2);
+          __syncthreads();
+        } else {
+          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u2, reinterpret_cast<float*>(u4), Yt, PREC);
+        }
         // stage 3: M u3 = f(y + a31 u1 + a32 u2) + (c31 u1 + c32 u2)/h
         for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A32, u2[i], fma(ROS_A31, u1[i], yv[i]));
         team_sync();
-        team_rhs(d, tab, pr, Yt, F, b, x);
+        team_rhs(d, tab, pr, Yt, F, b);
         for (int i = tid; i < n; i += P)
           u3[i] = fma(ROS_C32 * ih, u2[i], fma(ROS_C31 * ih, u1[i], F[i]));
         team_sync();
-        if (tid < 32) warp_lu_solve(M, n, piv, invd, u3);
-        __syncthreads();
+        if (PREC == 0) {
+          if (tid < 32) warp_lu_solve(M, n, piv, invd, u3);
+          __syncthreads();
+        } else {
+          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u3, reinterpret_cast<float*>(u4), Yt, PREC);
+        }
         // stage 4: same argument as stage 3 (a4j = a3j, a43 = 0), so f is reused
         for (int i = tid; i < n; i += P)
           u4[i] = fma(ROS_C43 * ih, u3[i], fma(ROS_C42 * ih, u2[i], fma(ROS_C41 * ih, u1[i], F[i])));
         team_sync();
-        if (tid < 32) warp_lu_solve(M, n, piv, invd, u4);
-        __syncthreads();
+        if (PREC == 0) {
+          if (tid < 32) warp_lu_solve(M, n, piv, invd, u4);
+          __syncthreads();
+        } else {
+          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u4, reinterpret_cast<float*>(F), Yt, PREC);
+        }
         // y* = y + sum m_i u_i (into Yt), e = sum E_i u_i (into F)
         int nf = 0;
         for (int i = tid; i < n; i += P) {
@@ -317,7 +384,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(DevMech d, int64
 // right-hand sides are evaluated by the team, so a reactor's working set
 // (8 n-vectors and one chunk of reaction scratch) stays in shared memory and
 // the number of steps of one reactor never holds back another.
-__global__ void __launch_bounds__(64) k_rkf45_team(DevMech d, int64_t N, const double* __restrict__ p,
+__global__ void __launch_bounds__(64) k_rkf45_team(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
                                                    double* __restrict__ y, const double* __restrict__ dt,
                                                    double* h_io, SolverParams sp, int32_t* steps,
                                                    int32_t* status, int32_t* queue) {
@@ -366,38 +433,38 @@ __global__ void __launch_bounds__(64) k_rkf45_team(DevMech d, int64_t N, const d
         const double hh = clamped ? tf - t : h;
         if (hh < hmin) { st = last_nf ? ST_NONFINITE : ST_HMIN; break; }
         // k_s = hh f(y + sum_j a_sj k_j)
-        team_rhs(d, d.tab, pr, yv, k0, b, x);
+        team_rhs(d, d.tab, pr, yv, k0, b);
         for (int i = tid; i < n; i += P) {
           k0[i] *= hh;
           yt[i] = fma(RK_A21, k0[i], yv[i]);
         }
         team_sync();
-        team_rhs(d, d.tab, pr, yt, k1, b, x);
+        team_rhs(d, d.tab, pr, yt, k1, b);
         for (int i = tid; i < n; i += P) {
           k1[i] *= hh;
           yt[i] = fma(RK_A32, k1[i], fma(RK_A31, k0[i], yv[i]));
         }
         team_sync();
-        team_rhs(d, d.tab, pr, yt, k2, b, x);
+        team_rhs(d, d.tab, pr, yt, k2, b);
         for (int i = tid; i < n; i += P) {
           k2[i] *= hh;
           yt[i] = fma(RK_A43, k2[i], fma(RK_A42, k1[i], fma(RK_A41, k0[i], yv[i])));
         }
         team_sync();
-        team_rhs(d, d.tab, pr, yt, k3, b, x);
+        team_rhs(d, d.tab, pr, yt, k3, b);
         for (int i = tid; i < n; i += P) {
           k3[i] *= hh;
           yt[i] = fma(RK_A54, k3[i], fma(RK_A53, k2[i], fma(RK_A52, k1[i], fma(RK_A51, k0[i], yv[i]))));
         }
         team_sync();
-        team_rhs(d, d.tab, pr, yt, k4, b, x);
+        team_rhs(d, d.tab, pr, yt, k4, b);
         for (int i = tid; i < n; i += P) {
           k4[i] *= hh;
           yt[i] = fma(RK_A65, k4[i],
                       fma(RK_A64, k3[i], fma(RK_A63, k2[i], fma(RK_A62, k1[i], fma(RK_A61, k0[i], yv[i])))));
         }
         team_sync();
-        team_rhs(d, d.tab, pr, yt, k5, b, x);
+        team_rhs(d, d.tab, pr, yt, k5, b);
         // y* = y + sum b k (into yt), e = sum (bh - b) k (into k1, whose weights are 0)
         int nf = 0;
         for (int i = tid; i < n; i += P) {
@@ -475,8 +542,9 @@ static int team_grid(K kernel, int threads, size_t smem, int64_t work, const Lau
   return (int)(g < 1 ? 1 : g);
 }
 
-size_t ros4_smem_bytes(int n, int S, int chunk) {
-  return sizeof(double) * ((size_t)n * n + 9 * (size_t)n + (n + 1) / 2 + team_bufs_doubles(S, chunk));
+size_t ros4_smem_bytes(int n, int S, int chunk, int prec) {
+  return sizeof(double) * ((size_t)n * n + 9 * (size_t)n + (n + 1) / 2 + team_bufs_doubles(S, chunk)) +
+         (prec ? sizeof(float) * (size_t)n * n : 0);
 }
 
 // Thread grid of the register-tiled LU for dimension n: G x G threads with
@@ -530,12 +598,12 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
                         int32_t* queue, cudaStream_t st, const LaunchCfg& cfg) {
   if (n <= 0) return cudaSuccess;
   const int nn = hm.d.n;
-  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.d.chunk);
+  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.d.chunk, cfg.precision);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   return with_grid(nn, [&](auto Gc, auto Tc) {
     constexpr int G = decltype(Gc)::value, T = decltype(Tc)::value;
-    auto kern = k_ros4<G, T>;
+    auto kern = cfg.precision == 2 ? k_ros4<G, T, 2> : (cfg.precision == 1 ? k_ros4<G, T, 1> : k_ros4<G, T, 0>);
     const int grid = team_grid(kern, G * G, smem, n, cfg);
     kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
     return cudaGetLastError();

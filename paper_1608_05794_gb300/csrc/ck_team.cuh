@@ -42,7 +42,7 @@ struct TeamBufs {
   double *X, *g2, *hRT, *cpR, *dcpR, *wd, *aT, *E, *u, *cs;  // [S]
   double *q, *dqT, *D;                                        // [chunk]
   double* P;                                                  // [chunk * JP] Jacobian partials
-  double* red;                                                // [32]
+  double* red;                                                // [48]
 };
 
 // Mixture quantities shared by the RHS and the Jacobian.
@@ -196,8 +196,9 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
 }
 
 // f(y) for one reactor.  y, f: shared memory, n = S + 1.
-static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab, double p, const double* y, double* f,
-                         TeamBufs& b, Mix& x) {
+static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab, double p,
+                                             const double* y, double* f, TeamBufs b) {
+  Mix x;
   team_species(m, p, y, b, x, false);
   team_sync();
   const int NC = m.n_chunks, CH = m.chunk;
@@ -346,21 +347,31 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
 // factor below the diagonal and the upper factor on and above it; piv[k] =
 // row exchanged with row k; invd[k] = 1 / U_kk.  Returns 0, or k+1 when pivot
 // k is zero or not finite (the same in every thread).  Ties pick the
-// smallest row index.  red: >= 3 G doubles of shared scratch.
-template <int G, int T>
-__device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, double* ub, double* red) {
+// smallest row index.  red: >= 2 G + G / 2 doubles of shared scratch.
+// Bits of |v| as an unsigned integer (orders like |v|; NaN above +inf).
+__device__ __forceinline__ unsigned long long abs_key(double v) {
+  return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ unsigned long long abs_key(float v) {
+  return (unsigned long long)((unsigned)__float_as_int(v) & 0x7fffffffu);
+}
+__device__ __forceinline__ unsigned long long inf_key(double) { return 0x7ff0000000000000ULL; }
+__device__ __forceinline__ unsigned long long inf_key(float) { return 0x7f800000ULL; }
+
+template <int G, int T, class F>
+__device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red) {
   const int tid = threadIdx.x, tr = tid / G, tc = tid - tr * G;
-  const unsigned long long ABS = 0x7fffffffffffffffULL, INFB = 0x7ff0000000000000ULL;
-  double a[T][T];
+  const unsigned long long INFB = inf_key(F(0));
+  F a[T][T];
 #pragma unroll
   for (int r = 0; r < T; ++r)
 #pragma unroll
     for (int c = 0; c < T; ++c) {
       const int i = tr + G * r, j = tc + G * c;
-      a[r][c] = (i < n && j < n) ? A[i * n + j] : 0.0;
+      a[r][c] = (i < n && j < n) ? A[i * n + j] : F(0);
     }
   unsigned long long* rk = reinterpret_cast<unsigned long long*>(red);  // [G] |candidate| bits
-  double* rs = red + G;                                                // [G] signed candidate
+  F* rs = reinterpret_cast<F*>(red + G);                               // [G] signed candidate
   int* ri = reinterpret_cast<int*>(red + 2 * G);                       // [G] candidate row
   int info = 0;
   for (int k = 0; k < n; ++k) {
@@ -368,7 +379,7 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
     // 1. candidates from the owners of column k (tc == kt, slot kq)
     if (tc == kt) {
       unsigned long long best = 0;
-      double bsig = 0.0;
+      F bsig = F(0);
       int bi = n;
 #pragma unroll
       for (int c = 0; c < T; ++c) {
@@ -376,7 +387,7 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
 #pragma unroll
         for (int r = 0; r < T; ++r) {
           const int i = tr + G * r;
-          const unsigned long long key = (unsigned long long)__double_as_longlong(a[r][c]) & ABS;
+          const unsigned long long key = abs_key(a[r][c]);
           if (i >= k && i < n && (bi == n || key > best)) {
             best = key;
             bsig = a[r][c];
@@ -390,7 +401,7 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
     }
     __syncthreads();
     unsigned long long best = 0;
-    double pv = 0.0;
+    F pv = F(0);
     int p = n;
     for (int t = 0; t < G; ++t) {
       if (ri[t] >= n) continue;
@@ -435,7 +446,7 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
     // 3. unscaled column k below the diagonal, the pivot row, the reciprocal
     if (tid == 0) {
       piv[k] = p;
-      invd[k] = 1.0 / pv;
+      invd[k] = F(1) / pv;
     }
     if (tc == kt) {
 #pragma unroll
@@ -462,7 +473,7 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
     __syncthreads();
     // one warp scales the multipliers
     if (tid < 32) {
-      const double ip = invd[k];
+      const F ip = invd[k];
       for (int i = k + 1 + tid; i < n; i += 32) lb[i] *= ip;
     }
     __syncthreads();
@@ -472,7 +483,7 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
       if (G * r + G - 1 <= k) continue;  // whole slot row above the block
       const int i = tr + G * r;
       const bool ri_ok = i > k && i < n;
-      const double li = ri_ok ? lb[i] : 0.0;
+      const F li = ri_ok ? lb[i] : F(0);
 #pragma unroll
       for (int c = 0; c < T; ++c) {
         if (G * c + G - 1 < k) continue;
@@ -500,14 +511,14 @@ __device__ int lu_reg(double* A, int n, int* piv, double* invd, double* lb, doub
 // earlier blocks is a matrix-vector product (one row per lane, four partial
 // sums in a fixed order), the diagonal block a substitution whose solved
 // value is broadcast by a shuffle.
-__device__ __forceinline__ void warp_lu_solve(const double* A, int n, const int* piv,
-                                              const double* invd, double* b) {
+template <class F>
+__device__ __forceinline__ void warp_lu_solve(const F* A, int n, const int* piv, const F* invd, F* b) {
   const int lane = threadIdx.x & 31;
   if (lane == 0) {
     for (int k = 0; k < n; ++k) {
       const int p = piv[k];
       if (p != k) {
-        const double t = b[k];
+        const F t = b[k];
         b[k] = b[p];
         b[p] = t;
       }
@@ -518,9 +529,9 @@ __device__ __forceinline__ void warp_lu_solve(const double* A, int n, const int*
   for (int B0 = 0; B0 < n; B0 += 32) {
     const int i = B0 + lane;
     const bool act = i < n;
-    double s0 = act ? b[i] : 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    F s0 = act ? b[i] : F(0), s1 = F(0), s2 = F(0), s3 = F(0);
     if (act) {
-      const double* Li = A + (size_t)i * n;
+      const F* Li = A + (size_t)i * n;
       int j = 0;
       for (; j + 4 <= B0; j += 4) {
         s0 = fma(-Li[j], b[j], s0);
@@ -530,10 +541,10 @@ __device__ __forceinline__ void warp_lu_solve(const double* A, int n, const int*
       }
       for (; j < B0; ++j) s0 = fma(-Li[j], b[j], s0);
     }
-    double s = (s0 + s1) + (s2 + s3);
+    F s = (s0 + s1) + (s2 + s3);
     const int m = min(32, n - B0);
     for (int jj = 0; jj < m; ++jj) {
-      const double yj = __shfl_sync(0xffffffffu, s, jj);
+      const F yj = __shfl_sync(0xffffffffu, s, jj);
       if (act && lane > jj) s = fma(-A[(size_t)i * n + B0 + jj], yj, s);
     }
     if (act) b[i] = s;
@@ -544,9 +555,9 @@ __device__ __forceinline__ void warp_lu_solve(const double* A, int n, const int*
     const int i = B1 + lane;
     const bool act = i < n;
     const int m = min(32, n - B1);
-    double s0 = act ? b[i] : 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    F s0 = act ? b[i] : F(0), s1 = F(0), s2 = F(0), s3 = F(0);
     if (act) {
-      const double* Ui = A + (size_t)i * n;
+      const F* Ui = A + (size_t)i * n;
       int j = B1 + 32;
       for (; j + 4 <= n; j += 4) {
         s0 = fma(-Ui[j], b[j], s0);
@@ -556,10 +567,10 @@ __device__ __forceinline__ void warp_lu_solve(const double* A, int n, const int*
       }
       for (; j < n; ++j) s0 = fma(-Ui[j], b[j], s0);
     }
-    double s = (s0 + s1) + (s2 + s3);
+    F s = (s0 + s1) + (s2 + s3);
     for (int jj = m - 1; jj >= 0; --jj) {
       if (lane == jj) s *= invd[i];
-      const double xj = __shfl_sync(0xffffffffu, s, jj);
+      const F xj = __shfl_sync(0xffffffffu, s, jj);
       if (act && lane < jj) s = fma(-A[(size_t)i * n + B1 + jj], xj, s);
     }
     if (act) b[i] = s;

@@ -263,3 +263,23 @@ def test_work_counts_scale(ck):
         assert w["lu_fp64"] > n ** 3 / 3
         assert w["ros4_step_fp64"] > w["lu_fp64"] + 3 * w["rhs_fp64"]
         assert w["rhs_exps"] >= len(m["rtype"])
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+@pytest.mark.parametrize("name,n", [("small", 128), ("medium", 48), ("large", 16)])
+def test_ros4_precision_form_matches_fp64_oracle(ck, name, n, precision):
+    # FP32 LU and stage solves with one or two FP64 refinement steps per
+    # solve; the final states must meet the same bar as the FP64 form
+    m, gm, om = _mech(ck, name)
+    cfg = CONFIGS[name]
+    y, p = reactor_states(name, n=n, seed_offset=29)
+    yg, sg, stg, _ = _integrate_gpu(ck, gm, ORA_ROS4, p, y, cfg["dt"], precision=precision)
+    yo, so, sto, _ = om.integrate(ORA_ROS4, p, y, cfg["dt"])
+    _assert_states_close(yg, yo, stg, sto)
+
+
+def test_precision_option_is_validated(ck):
+    m, gm, om = _mech(ck, "small")
+    y, p = reactor_states("small", n=4)
+    with pytest.raises(ck.CKError, match="precision"):
+        _integrate_gpu(ck, gm, ORA_RKF45, p, y, 1e-5, precision=1)
