@@ -418,6 +418,99 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def waste(steps: np.ndarray, P: int = 32) -> dict:
+    """Eq. waste of the paper over consecutive work units of P reactors:
+    W_j = 1 - sum_i N_i / (P max_i N_i), N_i = attempted steps of reactor i."""
+    n = (len(steps) // P) * P
+    if n == 0:
+        return {"P": P, "mean": None, "frac_below_1pct": None}
+    N = steps[:n].reshape(-1, P).astype(np.float64)
+    mx = N.max(axis=1)
+    W = 1.0 - N.sum(axis=1) / (P * np.where(mx > 0, mx, 1.0))
+    return {"P": P, "mean": float(W.mean()), "frac_below_1pct": float((W < 0.01).mean())}
+
+
+def run_batch(args):
+    """Mixed workload: the three mechanisms 50/35/15 over 200000 reactors,
+    half near ignition, dt log-uniform 1e-6..1e-4 s.  For RKF45 and ROS4:
+    (a) the plain form, one launch per mechanism in sequence (RKF45 also in
+    the paper's one-thread-per-reactor SIMT mapping), and (b) the batching
+    form: the three groups as persistent work-queue kernels on forked
+    branches, heaviest first, captured in a CUDA graph and replayed, with the
+    default launch shapes and with autotuned ones."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from paper_1608_05794_gb300 import autotune
+    from synth.configs import CONFIGS, load_mechanism, mixed_batch
+    groups = mixed_batch(n=args.batch_reactors)
+    mdicts = {nm: load_mechanism(CONFIGS[nm]["mech"]) for nm, *_ in groups}
+    mechs = {nm: ck.load_mechanism(mdicts[nm]) for nm in mdicts}
+    dev = [dict(name=nm, y=torch.as_tensor(y, device="cuda"), p=torch.as_tensor(p, device="cuda"),
+                dt=torch.as_tensor(dt, device="cuda")) for nm, y, p, dt in groups]
+    total = sum(g["y"].shape[0] for g in dev)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / 1e3
+
+    res = {}
+    for method, mname in ((1, "rkf45"), (0, "ros4")):
+        fn = ck.integrate_ros4 if method == 0 else ck.integrate_rkf45
+        forms = {"plain_team": dict(form=2)} if method == 0 else {"simt_thread": dict(form=1),
+                                                                  "plain_team": dict(form=2)}
+        out = {}
+        base_y = None
+        for fname, kw in forms.items():
+            ys = [g["y"].clone() for g in dev]
+            sts = [torch.empty(g["y"].shape[0], dtype=torch.int32, device="cuda") for g in dev]
+            stp = [torch.empty((g["y"].shape[0], 2), dtype=torch.int32, device="cuda") for g in dev]
+
+            def run_seq():
+                for g, yy, st, sp in zip(dev, ys, sts, stp):
+                    fn(mechs[g["name"]], g["p"], yy, g["dt"], st, steps=sp, opts=ck.SolverOpts.make(**kw))
+            t = timed(run_seq)
+            steps_all = np.concatenate([sp.cpu().numpy().sum(1) for sp in stp])
+            out[fname] = {"s": t, "reactors_per_s": total / t,
+                          "all_ok": all(bool((st == 0).all().item()) for st in sts), "waste": waste(steps_all)}
+            if fname == "plain_team":
+                base_y = [yy.cpu().numpy() for yy in ys]
+        tuned = {}
+        for g in dev:
+            k = min(args.tune_sample, g["y"].shape[0])
+            tuned[g["name"]] = autotune.tune(mechs[g["name"]], mdicts[g["name"]], method, g["p"][:k], g["y"][:k],
+                                             g["dt"][:k], sample=k)
+        for gname, use_tuned in (("graph_groups", False), ("graph_tuned_groups", True)):
+            ys = [g["y"].clone() for g in dev]
+            sts = [torch.empty(g["y"].shape[0], dtype=torch.int32, device="cuda") for g in dev]
+            specs = [dict(mech=mechs[g["name"]], p=g["p"], y=yy, dt=g["dt"], status=st,
+                          opts=ck.SolverOpts.make(**(tuned[g["name"]] if use_tuned else {"form": 2})))
+                     for g, yy, st in zip(dev, ys, sts)]
+            ck.integrate_groups(method, specs, use_graph=True)  # capture
+            torch.cuda.synchronize()
+            for yy, g in zip(ys, dev):
+                yy.copy_(g["y"])
+            t = timed(lambda: ck.integrate_groups(method, specs, use_graph=True))
+            same = all(np.array_equal(yy.cpu().numpy(), b) for yy, b in zip(ys, base_y))
+            out[gname] = {"s": t, "reactors_per_s": total / t,
+                          "all_ok": all(bool((st == 0).all().item()) for st in sts),
+                          "results_equal_plain_bitwise": same}
+            if use_tuned:
+                out[gname]["tuned"] = {nm: tuned[nm] for nm in tuned}
+        res[mname] = out
+    ck.graph_cache_clear()
+    line = {"mode": "batch", "metric": METRIC, "reactors": total,
+            "workload": "small/medium/large stand-ins 50/35/15, half near ignition, T U[900,2800] K, dt "
+                        "log-uniform 1e-6-1e-4 s, rtol 1e-9 atol 1e-12",
+            "groups": {g["name"]: int(g["y"].shape[0]) for g in dev}, "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(args):
     """A small case of one kernel for ncu (warm-up launches, then 3 launches)."""
     import torch
@@ -459,7 +552,9 @@ def main():
                     help="profiling only: launch one kernel a few times on a small batch, print no bench line")
     ap.add_argument("--reactors", type=int, default=2048, help="batch size of --profile-case")
     ap.add_argument("--dt", type=float, default=None, help="dt of --profile-case (default: the workload's)")
-    ap.add_argument("--mode", choices=["bench", "serve"], default="bench")
+    ap.add_argument("--mode", choices=["bench", "serve", "batch"], default="bench")
+    ap.add_argument("--batch-reactors", type=int, default=200000, help="batch: reactors of the mixed workload")
+    ap.add_argument("--tune-sample", type=int, default=4096, help="batch: reactors timed per autotuner candidate")
     ap.add_argument("--requests", type=int, default=12, help="serve: requests in the trace")
     ap.add_argument("--rate", type=float, default=500.0, help="serve: Poisson arrival rate, requests/s")
     ap.add_argument("--budget-gb", type=int, default=64, help="serve: HBM budget of the server")
@@ -468,6 +563,8 @@ def main():
     args = ap.parse_args()
     if args.mode == "serve":
         run_serve(args)
+    elif args.mode == "batch":
+        run_batch(args)
     elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":

@@ -125,6 +125,9 @@ typedef struct {
   int32_t variant;  /* 0: as many resident CTAs / blocks per SM as fit; > 0: cap per SM */
   int32_t form;     /* RKF45 mapping: 0 automatic, 1 one thread per reactor (shallow),
                        2 one CTA per reactor (deep); ROS4 always uses one CTA per reactor */
+  int32_t team;     /* ROS4 thread grid of a reactor team: 0 automatic, 8 (8x8 threads, n <= 56)
+                       or 16 (16x16 threads, n <= 112) */
+  int32_t pad;
 } ck_solver_opts;
 
 /* Fills *opts with rtol 1e-9, atol 1e-12, h0 0, fixed_h 0, max_steps 100000. */
@@ -182,6 +185,34 @@ int ck_integrate_ros4(const ck_mech* mech, int64_t n, const double* p, double* y
 int ck_integrate_rkf45(const ck_mech* mech, int64_t n, const double* p, double* y, const double* dt,
                        double* h_inout, const ck_solver_opts* opts, int32_t* steps, int32_t* status,
                        void* stream);
+
+/* ---------------------------------------------------------------- mixed batches
+ * Several groups of reactors, each on its own mechanism, integrated in one
+ * call (no counterpart in the paper, which runs one mechanism at a time).
+ * Every group runs as a persistent work-queue kernel on a branch forked from
+ * `stream`, launched in decreasing order of work_weight (or, when 0, of
+ * reactors x the cost of one step of the method from ck_count_work) at full
+ * occupancy, so the next group's CTAs take over SMs as the previous group's
+ * drain; opts.variant > 0 caps a group's resident CTAs per SM instead.  With use_graph != 0 the fork / kernels / join sequence
+ * is captured into a CUDA graph on the first call and replayed on later
+ * calls with byte-identical arguments (the cache holds 8 graphs; the input
+ * arrays may change contents, not addresses).  Device pointers only. */
+typedef struct {
+  const ck_mech* mech;
+  int64_t n;
+  const double* p;
+  double* y;
+  const double* dt;
+  double* h_inout;   /* may be NULL */
+  int32_t* steps;    /* may be NULL */
+  int32_t* status;
+  ck_solver_opts opts;
+  double work_weight;
+} ck_group;
+int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups, int32_t use_graph,
+                        void* stream);
+/* Free every cached graph (synchronizes the device). */
+int ck_graph_cache_clear(void);
 
 /* ---------------------------------------------------------------- serving
  * A request server for reactor batches that arrive over time (continuous

@@ -18,7 +18,8 @@ from .build import LIB, build
 
 __all__ = [
     "Mechanism", "load_mechanism", "rhs", "jacobian", "lu_factor", "lu_solve", "integrate_ros4",
-    "integrate_rkf45", "integrate_ros4_noalloc", "count_work", "Server", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
+    "integrate_rkf45", "integrate_ros4_noalloc", "count_work", "Server", "integrate_groups", "Group",
+    "graph_cache_clear", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
 ]
 
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "HMIN", 3: "NONFINITE", 4: "SINGULAR", 5: "BADINPUT"}
@@ -49,12 +50,20 @@ class MechDesc(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h0", C.c_double), ("fixed_h", C.c_double),
                 ("max_steps", C.c_int32), ("precision", C.c_int32), ("variant", C.c_int32),
-                ("form", C.c_int32)]
+                ("form", C.c_int32), ("team", C.c_int32), ("pad", C.c_int32)]
 
     @classmethod
     def make(cls, rtol=1e-9, atol=1e-12, h0=0.0, fixed_h=0.0, max_steps=100000, precision=0, variant=0,
-             form=0):
-        return cls(rtol, atol, h0, fixed_h, max_steps, precision, variant, form)
+             form=0, team=0):
+        return cls(rtol, atol, h0, fixed_h, max_steps, precision, variant, form, team, 0)
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+
+
+class Group(C.Structure):
+    _fields_ = [("mech", C.c_void_p), ("n", C.c_int64), ("p", _DP), ("y", _DP), ("dt", _DP), ("h_inout", _DP),
+                ("steps", _DP), ("status", _DP), ("opts", SolverOpts), ("work_weight", C.c_double)]
 
 
 class WorkCounts(C.Structure):
@@ -82,6 +91,7 @@ def _bind():
     L.ck_integrate_ros4_noalloc.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, _DP, C.POINTER(SolverOpts), _DP,
                                             _DP, _DP]
     L.ck_count_work.argtypes = [C.c_void_p, C.POINTER(WorkCounts)]
+    L.ck_integrate_groups.argtypes = [C.c_int32, C.c_int32, C.POINTER(Group), C.c_int32, _DP]
     L.ck_server_create.argtypes = [C.c_size_t, C.c_int32, C.c_int64, C.POINTER(C.c_void_p)]
     L.ck_submit.argtypes = [C.c_void_p, C.c_void_p, C.c_int32, C.c_int64, _DP, _DP, _DP, C.POINTER(SolverOpts),
                             _DP, _DP, C.POINTER(C.c_uint64)]
@@ -250,6 +260,31 @@ def integrate_ros4_noalloc(mech, p, y, dt, status, h_inout=None, steps=None, opt
     tensors only; calls on one device must not overlap on the GPU."""
     _integrate(_lib.ck_integrate_ros4_noalloc, "ck_integrate_ros4_noalloc", mech, p, y, dt, status, h_inout,
                steps, opts, stream)
+
+
+def integrate_groups(method, groups, use_graph=True, stream=None):
+    """Integrate several (mech, p, y, dt, status, steps, opts, weight) groups in
+    one call (ck_integrate_groups); device tensors only."""
+    arr = (Group * len(groups))()
+    keep = []
+    first = None
+    for g, spec in zip(arr, groups):
+        mech, p, y, dt, status = spec["mech"], spec["p"], spec["y"], spec["dt"], spec["status"]
+        first = first if first is not None else y
+        g.mech = mech.h
+        g.n = y.shape[0]
+        g.p, g.y, g.dt, g.status = _ptr(p), _ptr(y), _ptr(dt), _ptr(status)
+        g.h_inout = _ptr(spec.get("h_inout"))
+        g.steps = _ptr(spec.get("steps"))
+        g.opts = spec.get("opts") or SolverOpts.make()
+        g.work_weight = float(spec.get("weight", 0.0))
+        keep.append(spec)
+    _check(_lib.ck_integrate_groups(int(method), len(groups), arr, int(bool(use_graph)), _stream(stream, first)),
+           "ck_integrate_groups")
+
+
+def graph_cache_clear():
+    _check(_lib.ck_graph_cache_clear(), "ck_graph_cache_clear")
 
 
 class Server:

@@ -581,11 +581,13 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
     return fail(CK_EINVAL, "opts.precision: 0 (FP64) for both methods; 1 or 2 (FP32 LU + 1 or 2 FP64 "
                            "refinement steps) for ROS4");
   if (o.form < 0 || o.form > 2) return fail(CK_EINVAL, "opts.form must be 0, 1 or 2");
+  if (!(o.team == 0 || o.team == 8 || o.team == 16)) return fail(CK_EINVAL, "opts.team must be 0, 8 or 16");
   if (int rc = check_device(m)) return rc;
   ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
   ck::LaunchCfg cfg;
   if (o.variant > 0) cfg.ctas_per_sm = o.variant;
   cfg.precision = o.precision;
+  cfg.grid_side = o.team;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const size_t nn = (size_t)m->hm.d.n;
   const bool host = is_host_ptr(p) || is_host_ptr(y) || is_host_ptr(dt) || is_host_ptr(h_io) ||

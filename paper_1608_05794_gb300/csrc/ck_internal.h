@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "ck_common.cuh"
@@ -37,6 +38,7 @@ struct LaunchCfg {
   int team_warps = 0;   // warps per reactor for team kernels (0: heuristic)
   int ctas_per_sm = 0;  // 0: as many as fit
   int precision = 0;    // ROS4 linear algebra: 0 FP64, 1 FP32 + FP64 refinement
+  int grid_side = 0;    // ROS4 team: 0 automatic, 8 or 16 threads per side
 };
 
 cudaError_t launch_rhs(const HostMech& hm, int64_t n, const double* p, const double* y, double* f,
@@ -62,6 +64,7 @@ int sm_count();
 
 // Record a failure message for ck_last_error() and return code.
 int set_error(int code, const char* msg);
+inline int set_error(int code, const std::string& msg) { return set_error(code, msg.c_str()); }
 
 // Allocation-free ROS4 (ck_integrate_ros4_noalloc): the work-queue counter
 // lives in a static device array of NOALLOC_SCRATCH_INTS ints.

@@ -550,7 +550,8 @@ size_t ros4_smem_bytes(int n, int S, int chunk, int prec) {
 // Thread grid of the register-tiled LU for dimension n: G x G threads with
 // T x T tiles (n <= G T).
 template <class F>
-static cudaError_t with_grid(int n, F f) {
+static cudaError_t with_grid(int n, F f, int side = 0) {
+  if (side == 16 && n <= 112) return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 7>{});
   if (n <= 56) return f(std::integral_constant<int, 8>{}, std::integral_constant<int, 7>{});
   if (n <= 112) return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 7>{});
   if (n <= 144) return f(std::integral_constant<int, 16>{}, std::integral_constant<int, 9>{});
@@ -607,7 +608,7 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
     const int grid = team_grid(kern, G * G, smem, n, cfg);
     kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
     return cudaGetLastError();
-  });
+  }, cfg.grid_side);
 }
 
 cudaError_t launch_rkf45_team(const HostMech& hm, int64_t n, const double* p, double* y,

@@ -170,6 +170,7 @@ void launch_chunk(ck_server* s, Slot& sl, Request* r) {
   ck::SolverParams sp{r->opts.rtol, r->opts.atol, r->opts.h0, r->opts.fixed_h, r->opts.max_steps};
   ck::LaunchCfg cfg;
   cfg.precision = r->opts.precision;
+  cfg.grid_side = r->opts.team;
   if (r->opts.variant > 0) cfg.ctas_per_sm = r->opts.variant;
   cudaError_t e = cudaStreamWaitEvent(sl.stream, r->ready, 0);
   if (e == cudaSuccess) {

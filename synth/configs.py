@@ -73,3 +73,40 @@ def reactor_states(cfg_name: str, n: int | None = None, seed_offset: int = 0):
     nn = cfg["n_reactors"] if n is None else n
     return draw_states(rng, m["names"], m["elem"], m["mw"], m["elements"], nn,
                        cfg["t_range"], cfg["p_range_atm"])
+
+
+# Mixed workload: the three mechanisms in one batch (50/35/15 split of
+# 200000 reactors), T U[900, 2800] K, half the reactors of each mechanism
+# drawn from its near-ignition states, dt log-uniform on [1e-6, 1e-4] s.
+MIXED = dict(n_reactors=200000, split=(("small", 0.50), ("medium", 0.35), ("large", 0.15)), seed=2003,
+             t_range=(900.0, 2800.0), p_range_atm=(1.0, 20.0), dt_range=(1e-6, 1e-4))
+
+
+def ignition_states(cfg_name: str):
+    """Stored near-ignition states (y, p) of a workload's mechanism."""
+    path = os.path.join(DATA_DIR, f"ignition_{CONFIGS[cfg_name]['mech']}.npz")
+    with np.load(path) as z:
+        return z["y"], z["p"]
+
+
+def mixed_batch(n: int | None = None, seed: int | None = None):
+    """Groups of the mixed workload: list of (cfg_name, y, p, dt)."""
+    from .draw import draw_states
+    total = MIXED["n_reactors"] if n is None else n
+    rng = np.random.default_rng(MIXED["seed"] if seed is None else seed)
+    counts = [int(round(total * f)) for _, f in MIXED["split"]]
+    counts[-1] = total - sum(counts[:-1])
+    groups = []
+    for (name, _), cnt in zip(MIXED["split"], counts):
+        m = load_mechanism(CONFIGS[name]["mech"])
+        half = cnt // 2
+        y1, p1 = draw_states(rng, m["names"], m["elem"], m["mw"], m["elements"], cnt - half, MIXED["t_range"],
+                             MIXED["p_range_atm"])
+        yi, pi = ignition_states(name)
+        idx = rng.integers(len(yi), size=half)
+        y = np.concatenate([y1, yi[idx]])
+        p = np.concatenate([p1, pi[idx]])
+        perm = rng.permutation(cnt)
+        dt = 10.0 ** rng.uniform(np.log10(MIXED["dt_range"][0]), np.log10(MIXED["dt_range"][1]), cnt)
+        groups.append((name, np.ascontiguousarray(y[perm]), np.ascontiguousarray(p[perm]), dt))
+    return groups

@@ -44,3 +44,17 @@ def test_states_seeded_and_normalised():
     assert np.all(y1[:, 1:] >= 0)
     assert np.all((y1[:, 0] >= 1000) & (y1[:, 0] <= 2500))
     assert np.all((p1 >= 101325) & (p1 <= 20 * 101325))
+
+
+def test_mixed_workload_structure():
+    from synth.configs import ignition_states, mixed_batch
+    groups = mixed_batch(n=2000, seed=1)
+    assert [g[0] for g in groups] == ["small", "medium", "large"]
+    assert [len(g[2]) for g in groups] == [1000, 700, 300]
+    for name, y, p, dt in groups:
+        assert np.all((dt >= 1e-6) & (dt <= 1e-4))
+        assert np.allclose(y[:, 1:].sum(1), 1.0, atol=1e-12)
+        yi, pi = ignition_states(name)
+        # half of every group comes from the stored near-ignition states
+        hit = sum(any(np.array_equal(row, t) for t in yi) for row in y)
+        assert hit == len(y) // 2
