@@ -40,6 +40,29 @@ def _rank_env():
         os.environ.get("LOCAL_RANK", "0"))
 
 
+def rank_states(workload: str, n: int, rank: int):
+    """Weak scaling: every rank integrates its own seeded batch of n reactors
+    (reactors are independent, so no data moves between ranks)."""
+    from synth.configs import reactor_states
+    return reactor_states(workload, n=n, seed_offset=1000 * rank)
+
+
+def max_over_ranks(x: float, world: int, device=None) -> float:
+    """The job's time is the slowest rank's (the only collective of a run)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank: float, world: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the job's time."""
+    return units_per_rank * world / seconds
+
+
 class ClockSampler:
     """nvidia-smi clock / throttle sampling during the timed region."""
 
@@ -189,7 +212,7 @@ def run_ours(args):
     gm = ck.load_mechanism(m)
     work = ck.count_work(gm)
     N = cfg["n_reactors"]
-    y_np, p_np = reactor_states(WORKLOAD, n=N, seed_offset=1000 * rank)
+    y_np, p_np = rank_states(WORKLOAD, N, rank)
     dev = torch.device("cuda", torch.cuda.current_device())
     y0 = torch.as_tensor(y_np, device=dev)
     p = torch.as_tensor(p_np, device=dev)
@@ -241,12 +264,8 @@ def run_ours(args):
     barrier()
     elapsed = t0.elapsed_time(t1) / 1e3
     clocks = sampler.stop() if sampler else None
-    if world > 1:
-        tt = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        elapsed = float(tt.item())
-    integrations = 2.0 * N * world * args.steps
-    value = integrations / elapsed
+    elapsed = max_over_ranks(elapsed, world, dev)
+    value = aggregate_rate(2.0 * N * args.steps, world, elapsed)
 
     # correctness guard: every reactor finished
     st_ok = int((st_ros == 0).sum().item()) == N and int((st_rk == 0).sum().item()) == N
@@ -311,8 +330,8 @@ def run_ours(args):
                 h2d += ph.nbytes + yw.nbytes + dth.nbytes
                 d2h += yw.nbytes + sth.nbytes
         barrier()
-        te = time.perf_counter() - te
-        e2e = {"value": 2.0 * N * world * args.e2e_steps / te, "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - te, world, dev)
+        e2e = {"value": aggregate_rate(2.0 * N * args.e2e_steps, world, te), "unit": UNIT,
                "h2d_bytes_per_step": h2d // args.e2e_steps, "d2h_bytes_per_step": d2h // args.e2e_steps,
                "steps": args.e2e_steps}
 
