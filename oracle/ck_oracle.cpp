@@ -18,6 +18,7 @@
 #include <algorithm>
 #include <atomic>
 #include <cmath>
+#include <limits>
 #include <complex>
 #include <functional>
 #include <thread>
@@ -394,7 +395,40 @@ struct System {
   int n;
   std::function<void(const double*, double*)> f;    // f(y)
   std::function<void(const double*, double*)> jac;  // J(y), n x n row-major
+  int jac_fd = 0;                                    // 1: forward differences instead of jac
+  double rtol = 0.0, atol = 0.0;                     // weights of the difference increments
 };
+
+// Number of right-hand-side evaluations made by the reactor systems (all
+// threads), so tests can check the evaluations a step costs.
+std::atomic<int64_t> g_rhs_evals(0);
+
+// Forward-difference Jacobian, the paper's choice for ROS4 (Sec. 5), built
+// as in CVODE's dense difference-quotient routine: with unit roundoff U,
+// weights w_i = 1/(atol + rtol |y_i|) and fnorm = WRMS_w(f(y)), the floor
+// s0 = 1000 |h| U n fnorm (1 when fnorm = 0); column j is
+//   (f(y + s_j e_j) - f(y)) / s_j,  s_j = max(sqrt(U) |y_j|, s0 / w_j).
+// f0 = f(y) is given (it is the first stage's right-hand side), so a
+// Jacobian costs n further evaluations.
+void jac_fd(const System& sys, const double* y, const double* f0, double h, double* J) {
+  const int n = sys.n;
+  const double U = std::numeric_limits<double>::epsilon();
+  double fn = 0.0;
+  for (int i = 0; i < n; ++i) {
+    const double v = f0[i] / (sys.atol + sys.rtol * std::fabs(y[i]));
+    fn += v * v;
+  }
+  fn = std::sqrt(fn / n);
+  const double s0 = (fn != 0.0) ? 1000.0 * std::fabs(h) * U * n * fn : 1.0;
+  std::vector<double> yj(y, y + n), fj(n);
+  for (int j = 0; j < n; ++j) {
+    const double sj = std::max(std::sqrt(U) * std::fabs(y[j]), s0 * (sys.atol + sys.rtol * std::fabs(y[j])));
+    yj[j] = y[j] + sj;
+    sys.f(yj.data(), fj.data());
+    for (int i = 0; i < n; ++i) J[(size_t)i * n + j] = (fj[i] - f0[i]) / sj;
+    yj[j] = y[j];
+  }
+}
 
 // RKF45 OneStep (Sec. 2, Eq. rk): k_i = h f(y + sum_j a_ij k_j);
 // ynew = y + sum b_j k_j; err = sum (bh_j - b_j) k_j.
@@ -427,9 +461,15 @@ void rkf45_step(const System& sys, const double* y, double h, double* ynew, doub
 // J is evaluated at y.  Returns nonzero when the iteration matrix is singular.
 int ros4_step(const System& sys, const double* y, double h, double* ynew, double* err) {
   const int n = sys.n;
-  std::vector<double> M((size_t)n * n), u((size_t)4 * n), yt(n), ft(n), rhs(n);
+  std::vector<double> M((size_t)n * n), u((size_t)4 * n), yt(n), ft(n), rhs(n), f0;
   std::vector<int> piv(n);
-  sys.jac(y, M.data());
+  if (sys.jac_fd) {
+    f0.resize(n);
+    sys.f(y, f0.data());
+    jac_fd(sys, y, f0.data(), h, M.data());
+  } else {
+    sys.jac(y, M.data());
+  }
   for (size_t i = 0; i < (size_t)n * n; ++i) M[i] = -M[i];
   for (int i = 0; i < n; ++i) M[(size_t)i * n + i] += 1.0 / (h * ROS_GAMMA);
   if (lu_factor(n, M.data(), piv.data()) != 0) return 1;
@@ -439,7 +479,8 @@ int ros4_step(const System& sys, const double* y, double h, double* ynew, double
       for (int j = 0; j < s; ++j) acc += ROS_A[s][j] * u[(size_t)j * n + i];
       yt[i] = acc;
     }
-    sys.f(yt.data(), ft.data());
+    if (s == 0 && sys.jac_fd) ft = f0;  // f(y), already evaluated for the differences
+    else sys.f(yt.data(), ft.data());
     for (int i = 0; i < n; ++i) {
       double acc = ft[i];
       for (int j = 0; j < s; ++j) acc += (ROS_C[s][j] / h) * u[(size_t)j * n + i];
@@ -592,7 +633,10 @@ System reactor_system(const Mech& m, double p) {
   System s;
   s.n = m.S + 1;
   const Mech* mp = &m;
-  s.f = [mp, p](const double* y, double* f) { rhs_t<double>(*mp, p, y, f, nullptr, nullptr, nullptr); };
+  s.f = [mp, p](const double* y, double* f) {
+    g_rhs_evals.fetch_add(1, std::memory_order_relaxed);
+    rhs_t<double>(*mp, p, y, f, nullptr, nullptr, nullptr);
+  };
   s.jac = [mp, p](const double* y, double* J) { jac_one(*mp, p, y, J, nullptr); };
   return s;
 }
@@ -613,6 +657,12 @@ System test_system(int problem, int dim, const double* params) {
   } else if (problem == 1) {
     s.f = [](const double* y, double* f) { f[0] = -y[0] * y[0]; };
     s.jac = [](const double* y, double* J) { J[0] = -2.0 * y[0]; };
+  } else if (problem == 3) {
+    s.f = [n](const double* y, double* f) { for (int i = 0; i < n; ++i) f[i] = -y[i] * y[i]; };
+    s.jac = [n](const double* y, double* J) {
+      for (int i = 0; i < n * n; ++i) J[i] = 0.0;
+      for (int i = 0; i < n; ++i) J[i * n + i] = -2.0 * y[i];
+    };
   } else {
     s.f = [P, n](const double* y, double* f) {
       for (int i = 0; i < n; ++i) {
@@ -754,6 +804,9 @@ void ora_integrate(const ora_mech* h, int32_t method, int64_t n, const double* p
       st = ORA_BADINPUT;
     } else {
       System sys = reactor_system(h->m, p[i]);
+      sys.jac_fd = opts->jac == 1;
+      sys.rtol = opts->rtol;
+      sys.atol = opts->atol;
       st = drive(sys, method, y + i * nn, dt[i], h_inout ? h_inout + i : nullptr, *opts, &acc, &rej);
     }
     status[i] = st;
@@ -781,6 +834,33 @@ void ora_test_onestep(int32_t problem, int32_t method, int32_t dim, const double
   System sys = test_system(problem, dim, params);
   if (method == ORA_ROS4) ros4_step(sys, y, h, ynew, err);
   else rkf45_step(sys, y, h, ynew, err);
+}
+
+void ora_jacobian_fd(const ora_mech* h, int64_t n, const double* p, const double* y, const double* hstep,
+                     double rtol, double atol, double* jac) {
+  const int nn = h->m.S + 1;
+  parallel_for(n, 0, [&](int64_t i) {
+    System sys = reactor_system(h->m, p[i]);
+    sys.rtol = rtol;
+    sys.atol = atol;
+    std::vector<double> f0(nn);
+    sys.f(y + i * nn, f0.data());
+    jac_fd(sys, y + i * nn, f0.data(), hstep[i], jac + (size_t)i * nn * nn);
+  });
+}
+
+void ora_test_jacobian_fd(int32_t problem, int32_t dim, const double* params, const double* y, double h,
+                          double rtol, double atol, double* jac) {
+  System sys = test_system(problem, dim, params);
+  sys.rtol = rtol;
+  sys.atol = atol;
+  std::vector<double> f0(sys.n);
+  sys.f(y, f0.data());
+  jac_fd(sys, y, f0.data(), h, jac);
+}
+
+int64_t ora_rhs_evals(int32_t reset) {
+  return reset ? g_rhs_evals.exchange(0) : g_rhs_evals.load();
 }
 
 int32_t ora_hardware_threads(void) { return (int32_t)std::max(1u, std::thread::hardware_concurrency()); }

@@ -44,7 +44,7 @@ def build_oracle(force: bool = False) -> str:
 
 class _Opts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h0", C.c_double),
-                ("fixed_h", C.c_double), ("max_steps", C.c_int32), ("reserved", C.c_int32)]
+                ("fixed_h", C.c_double), ("max_steps", C.c_int32), ("jac", C.c_int32)]
 
 
 def _p(a, ct):
@@ -89,10 +89,20 @@ class Oracle:
                                          C.POINTER(_Opts), _IP, _IP]
         L.ora_test_onestep.argtypes = [C.c_int32, C.c_int32, C.c_int32, _DP, _DP, C.c_double, _DP, _DP]
         L.ora_hardware_threads.restype = C.c_int32
+        L.ora_jacobian_fd.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, C.c_double, C.c_double, _DP]
+        L.ora_test_jacobian_fd.argtypes = [C.c_int32, C.c_int32, _DP, _DP, C.c_double, C.c_double, C.c_double,
+                                           _DP]
+        L.ora_rhs_evals.restype = C.c_int64
+        L.ora_rhs_evals.argtypes = [C.c_int32]
 
     @staticmethod
-    def opts(rtol=1e-9, atol=1e-12, h0=0.0, fixed_h=0.0, max_steps=100000):
-        return _Opts(rtol, atol, h0, fixed_h, max_steps, 0)
+    def opts(rtol=1e-9, atol=1e-12, h0=0.0, fixed_h=0.0, max_steps=100000, jac=0):
+        """jac: ROS4 Jacobian, 0 analytic (Sec. 6), 1 forward differences (Sec. 5)."""
+        return _Opts(rtol, atol, h0, fixed_h, max_steps, jac)
+
+    def rhs_evals(self, reset: bool = False) -> int:
+        """Right-hand-side evaluations made by integrate() since the last reset."""
+        return int(self.lib.ora_rhs_evals(1 if reset else 0))
 
     def hardware_threads(self) -> int:
         return int(self.lib.ora_hardware_threads())
@@ -121,6 +131,15 @@ class Oracle:
         self.lib.ora_test_integrate(problem, method, dim, _p(params, C.c_double), _p(y, C.c_double),
                                     float(dt), C.byref(o), _p(steps, C.c_int32), _p(st, C.c_int32))
         return y, steps, int(st[0])
+
+    def test_jacobian_fd(self, problem, params, y, h, rtol=1e-9, atol=1e-12):
+        """Forward-difference Jacobian (Sec. 5) of a test problem at y, step size h."""
+        params = np.ascontiguousarray(params, dtype=np.float64).ravel()
+        y = np.ascontiguousarray(y, dtype=np.float64).ravel()
+        J = np.zeros((y.size, y.size))
+        self.lib.ora_test_jacobian_fd(problem, y.size, _p(params, C.c_double), _p(y, C.c_double), float(h),
+                                      float(rtol), float(atol), _p(J, C.c_double))
+        return J
 
     def test_onestep(self, problem, method, params, y0, h):
         params = np.ascontiguousarray(params, dtype=np.float64).ravel()
@@ -220,6 +239,17 @@ class OracleMech:
         self.o.lib.ora_jacobian(self.h, y.shape[0], _p(p, C.c_double), _p(y, C.c_double),
                                 _p(J, C.c_double), _p(G, C.c_double) if gross else None)
         return (J, G) if gross else J
+
+    def jacobian_fd(self, p, y, h, rtol=1e-9, atol=1e-12):
+        """Forward-difference Jacobians (Sec. 5) at step sizes h, as ROS4 with jac=1 builds them."""
+        y = np.ascontiguousarray(y, np.float64).reshape(-1, self.n)
+        nr = y.shape[0]
+        p = np.ascontiguousarray(np.broadcast_to(np.asarray(p, np.float64), (nr,)))
+        h = np.ascontiguousarray(np.broadcast_to(np.asarray(h, np.float64), (nr,)))
+        J = np.zeros((nr, self.n, self.n))
+        self.o.lib.ora_jacobian_fd(self.h, nr, _p(p, C.c_double), _p(y, C.c_double), _p(h, C.c_double),
+                                   float(rtol), float(atol), _p(J, C.c_double))
+        return J
 
     def integrate(self, method, p, y, dt, h_inout=None, nthreads=0, **kw):
         """Integrate every reactor over [0, dt].  Returns (y, steps[n,2], status[n], h)."""

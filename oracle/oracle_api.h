@@ -67,7 +67,7 @@ typedef struct {
   double h0;       /* > 0: initial step; 0: EstimateH0 */
   double fixed_h;  /* > 0: constant step, every step accepted (order tests) */
   int32_t max_steps;
-  int32_t reserved;
+  int32_t jac;     /* ROS4 Jacobian: 0 analytic (Sec. 6), 1 forward differences (Sec. 5) */
 } ora_opts;
 
 enum { ORA_OK = 0, ORA_MAXSTEPS = 1, ORA_HMIN = 2, ORA_NONFINITE = 3, ORA_SINGULAR = 4,
@@ -86,13 +86,28 @@ void ora_integrate(const ora_mech* m, int32_t method, int64_t n, const double* p
 /* Test problems with closed-form solutions, run through the same steppers
  * and driver.  problem 0: y' = diag(lam) y (dim = len(lam)); problem 1:
  * scalar y' = -y^2; problem 2: dense linear y' = A y with A = params
- * (dim x dim). */
+ * (dim x dim); problem 3: dim uncoupled copies y_i' = -y_i^2. */
 void ora_test_integrate(int32_t problem, int32_t method, int32_t dim, const double* params,
                         double* y, double dt, const ora_opts* opts, int32_t* steps,
                         int32_t* status);
 /* One step of size h from y (no control): ynew and the error vector. */
 void ora_test_onestep(int32_t problem, int32_t method, int32_t dim, const double* params,
                       const double* y, double h, double* ynew, double* err);
+
+/* Forward-difference Jacobians (Sec. 5, CVODE's difference quotients), one
+ * per reactor at step size hstep[i] with the weights 1/(atol + rtol |y|):
+ * the matrix ROS4 uses when ora_opts.jac = 1. */
+void ora_jacobian_fd(const ora_mech* m, int64_t n, const double* p, const double* y, const double* hstep,
+                     double rtol, double atol, double* jac);
+
+/* The same forward-difference Jacobian for a test problem (see
+ * ora_test_integrate) at y with step size h. */
+void ora_test_jacobian_fd(int32_t problem, int32_t dim, const double* params, const double* y, double h,
+                          double rtol, double atol, double* jac);
+
+/* Right-hand-side evaluations made by ora_integrate's reactor systems since
+ * the last reset (all threads); reset != 0 returns the count and zeroes it. */
+int64_t ora_rhs_evals(int32_t reset);
 
 int32_t ora_hardware_threads(void);
 
