@@ -127,7 +127,8 @@ typedef struct {
                        2 one CTA per reactor (deep); ROS4 always uses one CTA per reactor */
   int32_t team;     /* ROS4 thread grid of a reactor team: 0 automatic, 8 (8x8 threads, n <= 56)
                        or 16 (16x16 threads, n <= 112) */
-  int32_t pad;
+  int32_t jac;      /* ROS4 Jacobian: 0 analytic (Sec. 6), 1 forward differences as the paper
+                       ran it (Sec. 5; see ck_jacobian_fd), n further RHS evaluations a step */
 } ck_solver_opts;
 
 /* Fills *opts with rtol 1e-9, atol 1e-12, h0 0, fixed_h 0, max_steps 100000. */
@@ -158,6 +159,18 @@ int ck_rhs(const ck_mech* mech, int64_t n, const double* p, const double* y, dou
  * reactor. */
 int ck_jacobian(const ck_mech* mech, int64_t n, const double* p, const double* y, double* jac,
                 void* stream);
+
+/* Forward-difference Jacobian, the paper's choice for ROS4 (Sec. 5: first-order
+ * forward differences following CVODE, S+1 right-hand-side evaluations per
+ * Jacobian), with CVODE's dense difference-quotient increments: unit roundoff
+ * U = 2^-52, weights w_c = 1/(atol + rtol |y_c|), fnorm = the weighted RMS
+ * norm of f(y), floor s0 = 1000 |h| U (S+1) fnorm (1 when fnorm = 0), and
+ * column c = (f(y + s_c e_c) - f(y)) / s_c with s_c = max(2^-26 |y_c|,
+ * s0 / w_c).  h[n] is the step size each matrix is for; jac as in
+ * ck_jacobian.  One CTA per reactor; host or device pointers (host arrays
+ * are staged through device memory and the call synchronises). */
+int ck_jacobian_fd(const ck_mech* mech, int64_t n, const double* p, const double* y, const double* h,
+                   double rtol, double atol, double* jac, void* stream);
 
 /* Batched dense LU with partial pivoting (the linear algebra of the ROS4
  * stages, Sec. 2).  a[batch][dim][dim] row-major, factored in place into the
@@ -291,6 +304,8 @@ typedef struct {
   double rhs_fp64, rhs_exps, jac_fp64, lu_fp64, solve_fp64;
   double ros4_step_fp64, rkf45_step_fp64;
   double rhs_bytes, integrate_bytes;
+  double ros4_fd_step_fp64;  /* one ROS4 step with the forward-difference Jacobian: S+2 RHS
+                                (f(y) and one per column) + 2 stage RHS, LU, 4 solves, vector work */
 } ck_work_counts;
 int ck_count_work(const ck_mech* mech, ck_work_counts* out);
 

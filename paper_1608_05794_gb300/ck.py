@@ -50,15 +50,15 @@ class MechDesc(C.Structure):
 class SolverOpts(C.Structure):
     _fields_ = [("rtol", C.c_double), ("atol", C.c_double), ("h0", C.c_double), ("fixed_h", C.c_double),
                 ("max_steps", C.c_int32), ("precision", C.c_int32), ("variant", C.c_int32),
-                ("form", C.c_int32), ("team", C.c_int32), ("pad", C.c_int32)]
+                ("form", C.c_int32), ("team", C.c_int32), ("jac", C.c_int32)]
 
     @classmethod
     def make(cls, rtol=1e-9, atol=1e-12, h0=0.0, fixed_h=0.0, max_steps=100000, precision=0, variant=0,
-             form=0, team=0):
-        return cls(rtol, atol, h0, fixed_h, max_steps, precision, variant, form, team, 0)
+             form=0, team=0, jac=0):
+        return cls(rtol, atol, h0, fixed_h, max_steps, precision, variant, form, team, jac)
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_ if k != "pad"}
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 class Group(C.Structure):
@@ -69,7 +69,7 @@ class Group(C.Structure):
 class WorkCounts(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("rhs_fp64", "rhs_exps", "jac_fp64", "lu_fp64", "solve_fp64",
                                            "ros4_step_fp64", "rkf45_step_fp64", "rhs_bytes",
-                                           "integrate_bytes")]
+                                           "integrate_bytes", "ros4_fd_step_fp64")]
 
 
 class ServerInfo(C.Structure):
@@ -84,6 +84,7 @@ def _bind():
     L.ck_mech_info.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_int32)]
     L.ck_rhs.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, _DP]
     L.ck_jacobian.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, _DP]
+    L.ck_jacobian_fd.argtypes = [C.c_void_p, C.c_int64, _DP, _DP, _DP, C.c_double, C.c_double, _DP, _DP]
     L.ck_lu_factor.argtypes = [C.c_int64, C.c_int32, _DP, _DP, _DP, _DP]
     L.ck_lu_solve.argtypes = [C.c_int64, C.c_int32, _DP, _DP, _DP, _DP]
     for f in (L.ck_integrate_ros4, L.ck_integrate_rkf45):
@@ -222,6 +223,14 @@ def jacobian(mech: Mechanism, p, y, out, stream=None):
     """Analytic Jacobians [n, S+1, S+1] (ck_jacobian)."""
     n = y.shape[0]
     _check(_lib.ck_jacobian(mech.h, n, _ptr(p), _ptr(y), _ptr(out), _stream(stream, y)), "ck_jacobian")
+    return out
+
+
+def jacobian_fd(mech: Mechanism, p, y, h, out, rtol=1e-9, atol=1e-12, stream=None):
+    """Forward-difference Jacobians [n, S+1, S+1] at step sizes h[n] (ck_jacobian_fd)."""
+    n = y.shape[0]
+    _check(_lib.ck_jacobian_fd(mech.h, n, _ptr(p), _ptr(y), _ptr(h), float(rtol), float(atol), _ptr(out),
+                               _stream(stream, y)), "ck_jacobian_fd")
     return out
 
 

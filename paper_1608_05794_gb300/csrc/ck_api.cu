@@ -509,6 +509,35 @@ int ck_jacobian(const ck_mech* m, int64_t n, const double* p, const double* y, d
   return e == cudaSuccess ? CK_OK : cuda_fail(e, "ck_jacobian");
 }
 
+int ck_jacobian_fd(const ck_mech* m, int64_t n, const double* p, const double* y, const double* h, double rtol,
+                   double atol, double* jac, void* stream) {
+  if (!m) return fail(CK_EINVAL, "mech is NULL");
+  if (n < 0) return fail(CK_EINVAL, "n < 0");
+  if (n == 0) return CK_OK;
+  if (!p || !y || !h || !jac) return fail(CK_EINVAL, "p, y, h and jac are required");
+  if (!(rtol > 0.0) || !(atol > 0.0)) return fail(CK_EINVAL, "need rtol > 0 and atol > 0");
+  if (int rc = check_device(m)) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t nn = (size_t)m->hm.d.n;
+  ck::LaunchCfg cfg;
+  const bool host = is_host_ptr(p) || is_host_ptr(y) || is_host_ptr(h) || is_host_ptr(jac);
+  if (!host) {
+    cudaError_t e = ck::launch_jacobian_fd(m->hm, n, p, y, h, rtol, atol, jac, st, cfg);
+    return e == cudaSuccess ? CK_OK : cuda_fail(e, "ck_jacobian_fd launch");
+  }
+  Staged sg(st);
+  const double* dp = sg.map(const_cast<double*>(p), n, true, false);
+  const double* dy = sg.map(const_cast<double*>(y), n * nn, true, false);
+  const double* dh = sg.map(const_cast<double*>(h), n, true, false);
+  double* dj = sg.map(jac, n * nn * nn, false, true);
+  if (sg.err == cudaSuccess) {
+    cudaError_t e = ck::launch_jacobian_fd(m->hm, n, dp, dy, dh, rtol, atol, dj, st, cfg);
+    if (e != cudaSuccess) sg.err = e;
+  }
+  cudaError_t e = sg.finish();
+  return e == cudaSuccess ? CK_OK : cuda_fail(e, "ck_jacobian_fd");
+}
+
 int ck_lu_factor(int64_t batch, int32_t dim, double* a, int32_t* piv, int32_t* info, void* stream) {
   if (batch < 0 || dim < 1 || dim > 128) return fail(CK_ERANGE, "need batch >= 0 and 1 <= dim <= 128");
   if (batch == 0) return CK_OK;
@@ -582,8 +611,10 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
                            "refinement steps) for ROS4");
   if (o.form < 0 || o.form > 2) return fail(CK_EINVAL, "opts.form must be 0, 1 or 2");
   if (!(o.team == 0 || o.team == 8 || o.team == 16)) return fail(CK_EINVAL, "opts.team must be 0, 8 or 16");
+  if (o.jac < 0 || o.jac > 1 || (o.jac != 0 && method != 0))
+    return fail(CK_EINVAL, "opts.jac: 0 (analytic) for both methods; 1 (forward differences) for ROS4");
   if (int rc = check_device(m)) return rc;
-  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
+  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps, o.jac};
   ck::LaunchCfg cfg;
   if (o.variant > 0) cfg.ctas_per_sm = o.variant;
   cfg.precision = o.precision;
@@ -708,7 +739,7 @@ int ck_integrate_ros4_noalloc(const ck_mech* m, int64_t n, const double* p, doub
     return fail(CK_EINVAL, "opts: need rtol > 0, atol > 0, max_steps >= 1, h0 >= 0, fixed_h >= 0");
   if (o.precision != 0) return fail(CK_EINVAL, "opts.precision: only 0 (FP64) is available");
   if (int rc = check_device(m)) return rc;
-  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
+  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps, o.jac};
   ck::LaunchCfg cfg;
   if (o.variant > 0) cfg.ctas_per_sm = o.variant;
   cudaError_t e = ck::launch_ros4_noalloc(m->hm, n, p, y, dt, h_inout, sp, steps, status,
@@ -728,6 +759,10 @@ int ck_count_work(const ck_mech* m, ck_work_counts* o) {
   o->ros4_step_fp64 = o->jac_fp64 + 3.0 * o->rhs_fp64 + o->lu_fp64 + 4.0 * o->solve_fp64 +
                       (double)n * n + 30.0 * n;
   o->rkf45_step_fp64 = 6.0 * o->rhs_fp64 + 40.0 * n;
+  // f(y), n difference columns (each an RHS, a subtract and a divide per
+  // entry), the fnorm and increments, then stages 2 and 3 as above
+  o->ros4_fd_step_fp64 = (n + 3.0) * o->rhs_fp64 + 2.0 * (double)n * n + 8.0 * n + o->lu_fp64 +
+                         4.0 * o->solve_fp64 + (double)n * n + 30.0 * n;
   o->rhs_bytes = 8.0 * (2 * n + 1);
   o->integrate_bytes = 8.0 * (2 * n + 2) + 4.0;
   return CK_OK;

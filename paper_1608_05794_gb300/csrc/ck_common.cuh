@@ -163,6 +163,7 @@ constexpr double RK_D1 = 16.0 / 135.0 - 25.0 / 216.0, RK_D3 = 6656.0 / 12825.0 -
 struct SolverParams {
   double rtol, atol, h0, fixed_h;
   int max_steps;
+  int jac;  // ROS4 Jacobian: 0 analytic, 1 forward differences
 };
 
 }  // namespace ck

@@ -62,7 +62,7 @@ double group_work(int method, const ck_group& g) {
 cudaError_t launch_group(int method, const ck_group& g, int32_t* queue, cudaStream_t st, int ctas_per_sm) {
   const ck::HostMech& hm = g.mech->hm;
   const ck_solver_opts& o = g.opts;
-  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps};
+  ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps, o.jac};
   ck::LaunchCfg cfg;
   cfg.precision = o.precision;
   cfg.ctas_per_sm = ctas_per_sm;
@@ -107,7 +107,7 @@ int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups
     if (g.mech->hm.device != dev) return ck::set_error(CK_EINVAL, "group mechanism loaded on another device");
     const ck_solver_opts& o = g.opts;
     if (!(o.rtol > 0.0) || !(o.atol > 0.0) || o.max_steps < 1 || o.precision < 0 || o.precision > 2 ||
-        (o.precision && method != 0) || o.form < 0 || o.form > 2 || !(o.team == 0 || o.team == 8 || o.team == 16))
+        (o.precision && method != 0) || o.jac < 0 || o.jac > 1 || (o.jac && method != 0) || o.form < 0 || o.form > 2 || !(o.team == 0 || o.team == 8 || o.team == 16))
       return ck::set_error(CK_EINVAL, "group " + std::to_string(i) + ": invalid options");
     for (const void* ptr : {(const void*)g.p, (const void*)g.y, (const void*)g.dt, (const void*)g.status,
                             (const void*)g.steps, (const void*)g.h_inout}) {

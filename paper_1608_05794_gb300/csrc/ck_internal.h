@@ -45,6 +45,8 @@ cudaError_t launch_rhs(const HostMech& hm, int64_t n, const double* p, const dou
                        cudaStream_t st);
 cudaError_t launch_jacobian(const HostMech& hm, int64_t n, const double* p, const double* y,
                             double* jac, cudaStream_t st, const LaunchCfg& cfg);
+cudaError_t launch_jacobian_fd(const HostMech& hm, int64_t n, const double* p, const double* y, const double* h,
+                               double rtol, double atol, double* jac, cudaStream_t st, const LaunchCfg& cfg);
 cudaError_t launch_lu_factor(int64_t batch, int dim, double* a, int32_t* piv, int32_t* info,
                              cudaStream_t st);
 cudaError_t launch_lu_solve(int64_t batch, int dim, const double* lu, const int32_t* piv,

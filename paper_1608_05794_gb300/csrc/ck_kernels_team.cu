@@ -44,6 +44,39 @@ __device__ __forceinline__ int team_next(int32_t* queue, int* slot) {
   return r;
 }
 
+// Forward-difference Jacobian (the paper's choice for ROS4, Sec. 5), with
+// the increments of CVODE's dense difference quotients: unit roundoff U,
+// weights w_i = 1/(atol + rtol |y_i|), fnorm = WRMS_w(f(y)), floor
+// s0 = 1000 |h| U n fnorm (1 when fnorm = 0), and column j =
+// (f(y + s_j e_j) - f(y)) / s_j with s_j = max(sqrt(U) |y_j|, s0 / w_j).
+// f0 = f(y) is computed here and reused as the first stage's f; the n
+// columns cost n team RHS evaluations.  Yt, F: n-vector scratch.
+static __device__ __noinline__ void team_jacobian_fd(const DevMech& d, const double* tab, double p,
+                                                     const double* y, double h, double rtol, double atol,
+                                                     double* f0, double* J, double* Yt, double* F, TeamBufs b) {
+  const int n = d.n;
+  team_rhs(d, tab, p, y, f0, b);
+  double s = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    const double v = f0[i] / (atol + rtol * fabs(y[i]));
+    s = fma(v, v, s);
+    Yt[i] = y[i];
+  }
+  const double fn = sqrt(team_sum(s, b.red) / n);
+  const double U = 2.220446049250313080847e-16;  // 2^-52
+  const double srur = 1.490116119384765625e-8;   // 2^-26 = sqrt(U)
+  const double s0 = (fn != 0.0) ? 1000.0 * fabs(h) * U * n * fn : 1.0;
+  for (int j = 0; j < n; ++j) {
+    const double sj = fmax(srur * fabs(y[j]), s0 * (atol + rtol * fabs(y[j])));
+    if (threadIdx.x == 0) Yt[j] = y[j] + sj;
+    team_sync();
+    team_rhs(d, tab, p, Yt, F, b);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) J[(size_t)i * n + j] = (F[i] - f0[i]) / sj;
+    if (threadIdx.x == 0) Yt[j] = y[j];
+    team_sync();
+  }
+}
+
 // ------------------------------------------------------------------ Jacobian
 __global__ void k_jacobian(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
                            const double* __restrict__ y, double* __restrict__ jac) {
@@ -58,6 +91,28 @@ __global__ void k_jacobian(const __grid_constant__ DevMech d, int64_t N, const d
     for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = y[r * n + i];
     __syncthreads();
     team_jacobian(d, d.tab, p[r], ys, fs, J, b, x);
+    for (int e = threadIdx.x; e < n * n; e += blockDim.x) jac[r * (int64_t)n * n + e] = J[e];
+    __syncthreads();
+  }
+}
+
+// Forward-difference Jacobians (one CTA per reactor), as ROS4 builds them
+// with the forward-difference option at step size h[r].
+__global__ void k_jacobian_fd(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
+                              const double* __restrict__ y, const double* __restrict__ h, double rtol,
+                              double atol, double* __restrict__ jac) {
+  extern __shared__ __align__(16) double sm[];
+  const int n = d.n;
+  double* J = sm;
+  double* ys = J + (size_t)n * n;
+  double* fs = ys + n;
+  double* yt = fs + n;
+  double* ft = yt + n;
+  TeamBufs b = carve_bufs(ft + n, d.S, d.chunk);
+  for (int64_t r = blockIdx.x; r < N; r += gridDim.x) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) ys[i] = y[r * n + i];
+    __syncthreads();
+    team_jacobian_fd(d, d.tab, p[r], ys, h[r], rtol, atol, fs, J, yt, ft, b);
     for (int e = threadIdx.x; e < n * n; e += blockDim.x) jac[r * (int64_t)n * n + e] = J[e];
     __syncthreads();
   }
@@ -255,7 +310,8 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
         const double hh = clamped ? tf - t : h;
         if (hh < hmin) { st = last_nf ? ST_NONFINITE : ST_HMIN; break; }
         // J and f at y; M = I/(hh gamma) - J; LU
-        team_jacobian(d, tab, pr, yv, F0, M, b, x);
+        if (sp.jac == 1) team_jacobian_fd(d, tab, pr, yv, hh, sp.rtol, sp.atol, F0, M, Yt, F, b);
+        else team_jacobian(d, tab, pr, yv, F0, M, b, x);
         const double dg = 1.0 / (hh * ROS_GAMMA);
         for (int e = tid; e < n * n; e += P) M[e] = -M[e];
         team_sync();
@@ -566,6 +622,17 @@ cudaError_t launch_jacobian(const HostMech& hm, int64_t n, const double* p, cons
   const int threads = hm.d.chunk;
   const int grid = team_grid(k_jacobian, threads, smem, n, cfg);
   k_jacobian<<<grid, threads, smem, st>>>(hm.d, n, p, y, jac);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobian_fd(const HostMech& hm, int64_t n, const double* p, const double* y, const double* h,
+                               double rtol, double atol, double* jac, cudaStream_t st, const LaunchCfg& cfg) {
+  if (n <= 0) return cudaSuccess;
+  const int nn = hm.d.n;
+  const size_t smem = sizeof(double) * ((size_t)nn * nn + 4 * nn + team_bufs_doubles(hm.S, hm.d.chunk));
+  const int threads = hm.d.chunk;
+  const int grid = team_grid(k_jacobian_fd, threads, smem, n, cfg);
+  k_jacobian_fd<<<grid, threads, smem, st>>>(hm.d, n, p, y, h, rtol, atol, jac);
   return cudaGetLastError();
 }
 

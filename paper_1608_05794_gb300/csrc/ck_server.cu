@@ -167,7 +167,7 @@ void launch_chunk(ck_server* s, Slot& sl, Request* r) {
   sl.req = r;
   const ck::HostMech& hm = r->mech->hm;
   const int nn = hm.d.n;
-  ck::SolverParams sp{r->opts.rtol, r->opts.atol, r->opts.h0, r->opts.fixed_h, r->opts.max_steps};
+  ck::SolverParams sp{r->opts.rtol, r->opts.atol, r->opts.h0, r->opts.fixed_h, r->opts.max_steps, r->opts.jac};
   ck::LaunchCfg cfg;
   cfg.precision = r->opts.precision;
   cfg.grid_side = r->opts.team;
@@ -332,9 +332,13 @@ int ck_submit(ck_server* s, const ck_mech* mech, int32_t method, int64_t n, cons
   r->steps = steps;
   if (opts) r->opts = *opts;
   else ck_default_opts(&r->opts);
-  if (r->opts.precision != 0 && method != 0) {
+  if ((r->opts.precision != 0 || r->opts.jac != 0) && method != 0) {
     delete r;
-    return srv_fail(CK_EINVAL, "opts.precision applies to ROS4 only");
+    return srv_fail(CK_EINVAL, "opts.precision and opts.jac apply to ROS4 only");
+  }
+  if (r->opts.jac < 0 || r->opts.jac > 1) {
+    delete r;
+    return srv_fail(CK_EINVAL, "opts.jac must be 0 or 1");
   }
   const bool h = host_ptr(p) || host_ptr(y) || host_ptr(dt) || host_ptr(status) || host_ptr(steps);
   const bool d = !host_ptr(p) && !host_ptr(y) && !host_ptr(dt) && !host_ptr(status) && !host_ptr(steps);
