@@ -33,7 +33,9 @@ struct Mech {
   int S = 0, R = 0;
   std::vector<double> mw, nasa, tmid, arrh, arrh0;
   std::vector<int> reac, prod, rtype, rev;
-  std::vector<double> eff;  // dense [R][S] third-body efficiencies (1 where unlisted)
+  std::vector<double> eff;       // dense [R][S] third-body efficiencies (1 where unlisted)
+  std::vector<double> arrh_rev;  // [R][3] explicit reverse (A, beta, Ea) where rev == 2
+  int reactor = 0;               // 0 constant pressure (p given), 1 constant volume (rho given)
 };
 
 double re(double x) { return x; }
@@ -85,7 +87,12 @@ void reaction(const Mech& m, int i, Sc T, const Sc* X, const Sc* h_RT, const Sc*
   r.kf = ar[0] * std::pow(T, ar[1]) * std::exp(-ar[2] / (R_GAS * T));
   r.kr = 0.0;
   r.Kc = 0.0;
-  if (m.rev[i]) {
+  if (m.rev[i] == 2) {
+    // explicit reverse Arrhenius coefficients (Sec. 3), in place of Eq. krev
+    const double* rr = &m.arrh_rev[i * 3];
+    r.kr = rr[0] * std::pow(T, rr[1]) * std::exp(-rr[2] / (R_GAS * T));
+    r.Kc = r.kf / r.kr;
+  } else if (m.rev[i]) {
     Sc sum = 0.0;  // sum_j (nu''_j - nu'_j) (S_j/R - H_j/(R T))
     int dnu = 0;
     for (int s = 0; s < 3; ++s) {
@@ -110,7 +117,10 @@ void reaction(const Mech& m, int i, Sc T, const Sc* X, const Sc* h_RT, const Sc*
       const double* a0 = &m.arrh0[i * 3];
       r.k0 = a0[0] * std::pow(T, a0[1]) * std::exp(-a0[2] / (R_GAS * T));
       r.Pr = r.k0 * r.M / r.kf;
-      r.c = r.Pr / (1.0 + r.Pr);
+      // P_r/(1+P_r), written as 1/(1 + 1/P_r) above P_r = 1 so that the
+      // complex-step twin keeps the derivative 1/(1+P_r)^2 free of cancellation
+      if (re(r.Pr) > 1.0) r.c = 1.0 / (1.0 + 1.0 / r.Pr);
+      else r.c = r.Pr / (1.0 + r.Pr);
     }
   }
   r.fwd = 1.0;
@@ -122,14 +132,17 @@ void reaction(const Mech& m, int i, Sc T, const Sc* X, const Sc* h_RT, const Sc*
   r.q = r.c * (r.kf * r.fwd - r.kr * r.rev);
 }
 
-// Mixture state of Sec. 3: mean molar mass, density from the ideal-gas law
-// p = rho (R/W) T, and molar concentrations [X_k] = rho Y_k / W_k.
+// Mixture state of Sec. 3: mean molar mass, density, and molar
+// concentrations [X_k] = rho Y_k / W_k.  Constant pressure: rho from the
+// ideal-gas law p = rho (R/W) T with the given p.  Constant volume: the
+// second argument is the (fixed) density itself.
 template <class Sc>
 void mixture(const Mech& m, double p, const Sc* y, Sc& Wbar, Sc& rho, Sc* X) {
   Sc sumYW = 0.0;
   for (int k = 0; k < m.S; ++k) sumYW += y[1 + k] / m.mw[k];
   Wbar = 1.0 / sumYW;
-  rho = p * Wbar / (R_GAS * y[0]);
+  if (m.reactor == 1) rho = p;
+  else rho = p * Wbar / (R_GAS * y[0]);
   for (int k = 0; k < m.S; ++k) X[k] = rho * y[1 + k] / m.mw[k];
 }
 
@@ -138,6 +151,8 @@ void mixture(const Mech& m, double p, const Sc* y, Sc& Wbar, Sc& rho, Sc* X) {
 //   dT/dt   = -(sum_k H_k wdot_k) / (rho cp),
 // with H_k the molar enthalpy and cp = sum_k Y_k cp_k / W_k the mass-based
 // mixture heat capacity (the printed Eq. tdot omits rho; dimensions need it).
+// Constant volume (Sec. 3: c_v for c_p and u_k for h_k): the molar internal
+// energy U_k = H_k - R T and c_v = sum_k Y_k (cp_k - R) / W_k in Eq. tdot.
 template <class Sc>
 void rhs_t(const Mech& m, double p, const Sc* y, Sc* f, Sc* wdot_out, Sc* q_out, double* gross) {
   const int S = m.S;
@@ -161,11 +176,12 @@ void rhs_t(const Mech& m, double p, const Sc* y, Sc* f, Sc* wdot_out, Sc* q_out,
       }
     }
   }
+  const double cv = (m.reactor == 1) ? 1.0 : 0.0;  // subtract R from cp and R T from H
   Sc cp = 0.0, sumHw = 0.0;
   double gT = 0.0;
   for (int k = 0; k < S; ++k) {
-    cp += y[1 + k] * (R_GAS * cp_R[k]) / m.mw[k];
-    sumHw += (R_GAS * T * h_RT[k]) * wdot[k];
+    cp += y[1 + k] * (R_GAS * (cp_R[k] - cv)) / m.mw[k];
+    sumHw += (R_GAS * T * (h_RT[k] - cv)) * wdot[k];
   }
   for (int k = 0; k < S; ++k) f[1 + k] = wdot[k] * m.mw[k] / rho;
   f[0] = -sumHw / (rho * cp);
@@ -175,7 +191,7 @@ void rhs_t(const Mech& m, double p, const Sc* y, Sc* f, Sc* wdot_out, Sc* q_out,
     double rr = std::abs(rho), cc = std::abs(cp);
     for (int k = 0; k < S; ++k) {
       gross[1 + k] = gw[k] * m.mw[k] / rr;
-      gT += std::abs(R_GAS * T * h_RT[k]) * gw[k];
+      gT += std::abs(R_GAS * T * (h_RT[k] - cv)) * gw[k];
     }
     gross[0] = gT / (rr * cc);
   }
@@ -184,12 +200,16 @@ void rhs_t(const Mech& m, double p, const Sc* y, Sc* f, Sc* wdot_out, Sc* q_out,
 // Analytic Jacobian of the same system, d f / d (T, Y_1..Y_S) at constant p.
 // Chain rule through rho(T, Y) and [X](rho, Y):
 //   d[X_k]/dT = -[X_k]/T,  d[X_k]/dY_j = rho/W_k delta_kj - [X_k] Wbar / W_j;
+// at constant volume rho is fixed: d[X_k]/dT = 0, d[X_k]/dY_j = rho/W_k delta_kj,
+// and the temperature row uses U_k = H_k - R T, c_v = sum Y_k (cp_k - R)/W_k;
 //   d ln k_f/dT = beta/T + Ea/(R T^2);  d ln K_c/dT = sum_j dnu_j (H_j/RT)/T - dnu/T;
+//   explicit reverse: d ln k_r/dT = beta_r/T + Ea_r/(R T^2);
 //   Lindemann: dc/dP_r = 1/(1+P_r)^2, d ln P_r/dT = d ln k0/dT - d ln k_inf/dT,
 //   dP_r/d[X_j] = eff_j k0 / k_inf.
 // gross (may be NULL) gets the same sums with every term in absolute value.
 void jac_one(const Mech& m, double p, const double* y, double* J, double* G) {
   const int S = m.S, n = S + 1;
+  const double cpf = (m.reactor == 1) ? 0.0 : 1.0;  // terms present only at constant pressure
   std::vector<double> X(S), cp_R(S), h_RT(S), s_R(S), dcp_R(S), wdot(S, 0.0);
   std::vector<double> dwdT(S, 0.0), dwdY((size_t)S * S, 0.0);
   std::vector<double> gwdT(S, 0.0), gwdY((size_t)S * S, 0.0), gw(S, 0.0);
@@ -235,7 +255,7 @@ void jac_one(const Mech& m, double p, const double* y, double* J, double* G) {
     const double* ar = &m.arrh[i * 3];
     double dlnkf = ar[1] / T + ar[2] / (R_GAS * T * T);
     double dlnKc = 0.0;
-    if (m.rev[i]) {
+    if (m.rev[i] == 1) {
       int dnu = 0;
       for (int s = 0; s < 3; ++s) {
         int j = m.prod[i * 3 + s];
@@ -247,6 +267,10 @@ void jac_one(const Mech& m, double p, const double* y, double* J, double* G) {
     }
     double dkf = r.kf * dlnkf;
     double dkr = r.kr * (dlnkf - dlnKc);
+    if (m.rev[i] == 2) {
+      const double* rr = &m.arrh_rev[i * 3];
+      dkr = r.kr * (rr[1] / T + rr[2] / (R_GAS * T * T));
+    }
     double dc_dT = 0.0;
     if (m.rtype[i] == 2) {
       const double* a0 = &m.arrh0[i * 3];
@@ -262,11 +286,11 @@ void jac_one(const Mech& m, double p, const double* y, double* J, double* G) {
       D += dqdX[j] * X[j];
       gD += gdqdX[j] * std::fabs(X[j]);
     }
-    double dqdT = dqdT_X - D / T;
-    double gdqdT = gdqdT_X + gD / T;
+    double dqdT = dqdT_X - cpf * D / T;
+    double gdqdT = gdqdT_X + cpf * gD / T;
     for (int j = 0; j < S; ++j) {
-      dqdY[j] = dqdX[j] * rho / m.mw[j] - (Wbar / m.mw[j]) * D;
-      gdqdY[j] = gdqdX[j] * rho / m.mw[j] + (Wbar / m.mw[j]) * gD;
+      dqdY[j] = dqdX[j] * rho / m.mw[j] - cpf * (Wbar / m.mw[j]) * D;
+      gdqdY[j] = gdqdX[j] * rho / m.mw[j] + cpf * (Wbar / m.mw[j]) * gD;
     }
     double gq = std::fabs(r.c) * gnet;
     for (int k = 0; k < S; ++k) {
@@ -283,48 +307,50 @@ void jac_one(const Mech& m, double p, const double* y, double* J, double* G) {
       }
     }
   }
-  // species rows: Y_k' = wdot_k W_k / rho
+  // species rows: Y_k' = wdot_k W_k / rho (rho depends on T and Y only at constant p)
   for (int k = 0; k < S; ++k) {
     double wk = m.mw[k];
-    J[(size_t)(1 + k) * n + 0] = wk / rho * dwdT[k] + wdot[k] * wk / (rho * T);
+    J[(size_t)(1 + k) * n + 0] = wk / rho * dwdT[k] + cpf * wdot[k] * wk / (rho * T);
     for (int j = 0; j < S; ++j)
       J[(size_t)(1 + k) * n + 1 + j] =
-          wk / rho * dwdY[(size_t)k * S + j] + wdot[k] * wk * Wbar / (rho * m.mw[j]);
+          wk / rho * dwdY[(size_t)k * S + j] + cpf * wdot[k] * wk * Wbar / (rho * m.mw[j]);
     if (G) {
-      G[(size_t)(1 + k) * n + 0] = wk / rho * gwdT[k] + gw[k] * wk / (rho * T);
+      G[(size_t)(1 + k) * n + 0] = wk / rho * gwdT[k] + cpf * gw[k] * wk / (rho * T);
       for (int j = 0; j < S; ++j)
         G[(size_t)(1 + k) * n + 1 + j] =
-            wk / rho * gwdY[(size_t)k * S + j] + gw[k] * wk * Wbar / (rho * m.mw[j]);
+            wk / rho * gwdY[(size_t)k * S + j] + cpf * gw[k] * wk * Wbar / (rho * m.mw[j]);
     }
   }
-  // temperature row: T' = -(sum_k H_k wdot_k) / (rho cp)
+  // temperature row: T' = -(sum_k E_k wdot_k) / (rho c) with E_k = H_k, c = cp
+  // (constant pressure) or E_k = U_k = H_k - R T, c = c_v (constant volume)
+  const double cv = 1.0 - cpf;
   double cpm = 0.0, dcpm = 0.0, Q = 0.0, gQ = 0.0;
   for (int k = 0; k < S; ++k) {
-    cpm += y[1 + k] * R_GAS * cp_R[k] / m.mw[k];
+    cpm += y[1 + k] * R_GAS * (cp_R[k] - cv) / m.mw[k];
     dcpm += y[1 + k] * R_GAS * dcp_R[k] / m.mw[k];
-    Q += R_GAS * T * h_RT[k] * wdot[k];
-    gQ += std::fabs(R_GAS * T * h_RT[k]) * gw[k];
+    Q += R_GAS * T * (h_RT[k] - cv) * wdot[k];
+    gQ += std::fabs(R_GAS * T * (h_RT[k] - cv)) * gw[k];
   }
   const double Tdot = -Q / (rho * cpm);
   const double gTdot = gQ / (rho * cpm);
   double dQdT = 0.0, gdQdT = 0.0;
   for (int k = 0; k < S; ++k) {
-    dQdT += R_GAS * cp_R[k] * wdot[k] + R_GAS * T * h_RT[k] * dwdT[k];
-    gdQdT += std::fabs(R_GAS * cp_R[k]) * gw[k] + std::fabs(R_GAS * T * h_RT[k]) * gwdT[k];
+    dQdT += R_GAS * (cp_R[k] - cv) * wdot[k] + R_GAS * T * (h_RT[k] - cv) * dwdT[k];
+    gdQdT += std::fabs(R_GAS * (cp_R[k] - cv)) * gw[k] + std::fabs(R_GAS * T * (h_RT[k] - cv)) * gwdT[k];
   }
-  J[0] = -dQdT / (rho * cpm) - Tdot * (-1.0 / T + dcpm / cpm);
-  if (G) G[0] = gdQdT / (rho * cpm) + gTdot * (1.0 / T + std::fabs(dcpm / cpm));
+  J[0] = -dQdT / (rho * cpm) - Tdot * (-cpf / T + dcpm / cpm);
+  if (G) G[0] = gdQdT / (rho * cpm) + gTdot * (cpf / T + std::fabs(dcpm / cpm));
   for (int j = 0; j < S; ++j) {
     double dQdY = 0.0, gdQdY = 0.0;
     for (int k = 0; k < S; ++k) {
-      dQdY += R_GAS * T * h_RT[k] * dwdY[(size_t)k * S + j];
-      gdQdY += std::fabs(R_GAS * T * h_RT[k]) * gwdY[(size_t)k * S + j];
+      dQdY += R_GAS * T * (h_RT[k] - cv) * dwdY[(size_t)k * S + j];
+      gdQdY += std::fabs(R_GAS * T * (h_RT[k] - cv)) * gwdY[(size_t)k * S + j];
     }
-    double dlog = R_GAS * cp_R[j] / (m.mw[j] * cpm) - Wbar / m.mw[j];
+    double dlog = R_GAS * (cp_R[j] - cv) / (m.mw[j] * cpm) - cpf * Wbar / m.mw[j];
     J[1 + j] = -dQdY / (rho * cpm) - Tdot * dlog;
     if (G)
       G[1 + j] = gdQdY / (rho * cpm) +
-                 gTdot * (std::fabs(R_GAS * cp_R[j] / (m.mw[j] * cpm)) + Wbar / m.mw[j]);
+                 gTdot * (std::fabs(R_GAS * (cp_R[j] - cv) / (m.mw[j] * cpm)) + cpf * Wbar / m.mw[j]);
   }
 }
 
@@ -706,8 +732,10 @@ ora_mech* ora_mech_create(int32_t S, int32_t R, const double* mw, const double* 
                           const double* tmid, const int32_t* reac, const int32_t* prod,
                           const double* arrh, const int32_t* rtype, const int32_t* rev,
                           const double* arrh0, const int32_t* eff_ptr, const int32_t* eff_sp,
-                          const double* eff_val) {
-  if (S <= 0 || R < 0) return nullptr;
+                          const double* eff_val, const double* arrh_rev, int32_t reactor) {
+  if (S <= 0 || R < 0 || reactor < 0 || reactor > 1) return nullptr;
+  for (int i = 0; i < R; ++i)
+    if (rev[i] < 0 || rev[i] > 2 || (rev[i] == 2 && !arrh_rev)) return nullptr;
   ora_mech* h = new ora_mech;
   Mech& m = h->m;
   m.S = S;
@@ -721,6 +749,8 @@ ora_mech* ora_mech_create(int32_t S, int32_t R, const double* mw, const double* 
   m.arrh0.assign(arrh0, arrh0 + (size_t)R * 3);
   m.rtype.assign(rtype, rtype + R);
   m.rev.assign(rev, rev + R);
+  m.reactor = reactor;
+  if (arrh_rev) m.arrh_rev.assign(arrh_rev, arrh_rev + (size_t)R * 3);
   m.eff.assign((size_t)R * S, 1.0);
   for (int i = 0; i < R; ++i)
     for (int e = eff_ptr[i]; e < eff_ptr[i + 1]; ++e) m.eff[(size_t)i * S + eff_sp[e]] = eff_val[e];

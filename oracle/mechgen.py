@@ -173,3 +173,29 @@ def make_mechanism(n_species, n_reactions, n_thirdbody, n_falloff, elements, see
         print(f"  {n_species} species, {len(rtype)} reactions; cap {lam_cap:g}/s rejected "
               f"{cap.rejected} of {cap.candidates} candidate reactions")
     return m
+
+
+def with_explicit_reverse(m: dict, frac: float = 0.25, seed: int = 4242,
+                          temps=(1000.0, 1700.0, 2500.0)) -> dict:
+    """A copy of mechanism m in which a random fraction of the reversible
+    reactions carries explicit reverse Arrhenius coefficients (Sec. 3)
+    instead of K_c.  Each explicit triple (A_r, beta_r, Ea_r) interpolates
+    the K_c-based reverse rate ln k_r(T) = ln A_r + beta_r ln T - Ea_r/(R T)
+    exactly at three temperatures, so the reverse rates (and the stiffness
+    cap they obey) stay close to the original ones.  Test input only."""
+    rng = np.random.default_rng(seed)
+    picked = synth.pick_reactions(rng, m["rev"], frac)
+    om = OracleMech(m)
+    lnkr = np.array([np.log(om.rate_coeffs(T)[2][picked]) for T in temps])  # [3, k]
+    R_GAS = 8.314462618
+    A = np.array([[1.0, np.log(T), -1.0 / (R_GAS * T)] for T in temps])
+    coef = np.linalg.solve(A, lnkr)  # rows: ln A_r, beta_r, Ea_r
+    out = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in m.items()}
+    out["rev"] = np.asarray(m["rev"]).astype(np.uint8).copy()
+    out["rev"][picked] = 2
+    arrh_rev = np.zeros((len(m["rev"]), 3))
+    arrh_rev[picked, 0] = np.exp(coef[0])
+    arrh_rev[picked, 1] = coef[1]
+    arrh_rev[picked, 2] = coef[2]
+    out["arrh_rev"] = arrh_rev
+    return out

@@ -72,7 +72,7 @@ class Oracle:
         L = self.lib
         L.ora_mech_create.restype = C.c_void_p
         L.ora_mech_create.argtypes = [C.c_int32, C.c_int32, _DP, _DP, _DP, _IP, _IP, _DP, _IP, _IP,
-                                      _DP, _IP, _IP, _DP]
+                                      _DP, _IP, _IP, _DP, _DP, C.c_int32]
         L.ora_mech_free.argtypes = [C.c_void_p]
         L.ora_thermo.argtypes = [C.c_void_p, C.c_double, _DP, _DP, _DP]
         L.ora_rate_coeffs.argtypes = [C.c_void_p, C.c_double, _DP, _DP, _DP, _DP]
@@ -155,9 +155,14 @@ class OracleMech:
     """A mechanism (dict of numpy arrays as from ``synth.load_mechanism``)
     loaded into the oracle."""
 
-    def __init__(self, mech: dict):
+    def __init__(self, mech: dict, reactor: int = 0):
+        """reactor 0: constant pressure (the per-reactor parameter p is the
+        pressure, Pa); 1: constant volume (p is the fixed density, kg/m^3).
+        Reactions with rev == 2 take explicit reverse Arrhenius coefficients
+        from mech["arrh_rev"] [R, 3]."""
         self.o = Oracle()
         m = mech
+        self.reactor = int(reactor)
         self.S = int(m["mw"].shape[0])
         self.R = int(m["reac"].shape[0])
         self.n = self.S + 1
@@ -174,6 +179,8 @@ class OracleMech:
             eff_ptr=np.ascontiguousarray(m["eff_ptr"], np.int32),
             eff_sp=np.ascontiguousarray(m["eff_sp"], np.int32),
             eff_val=np.ascontiguousarray(m["eff_val"], np.float64),
+            arrh_rev=np.ascontiguousarray(m["arrh_rev"] if "arrh_rev" in m else np.zeros((len(m["reac"]), 3)),
+                                          np.float64),
         )
         k = self._keep
         if k["eff_sp"].size == 0:
@@ -183,7 +190,8 @@ class OracleMech:
         self.h = self.o.lib.ora_mech_create(
             self.S, self.R, _p(k["mw"], d), _p(k["nasa"], d), _p(k["tmid"], d), _p(k["reac"], i),
             _p(k["prod"], i), _p(k["arrh"], d), _p(k["rtype"], i), _p(k["rev"], i), _p(k["arrh0"], d),
-            _p(k["eff_ptr"], i), _p(k["eff_sp"], i), _p(k["eff_val"], d))
+            _p(k["eff_ptr"], i), _p(k["eff_sp"], i), _p(k["eff_val"], d),
+            _p(k["arrh_rev"], d) if k["arrh_rev"].size else None, self.reactor)
         if not self.h:
             raise ValueError("oracle rejected the mechanism")
 

@@ -23,13 +23,17 @@ typedef struct ora_mech ora_mech;
 /* Build a mechanism from plain arrays (copied).  reac/prod are [R][3] species
  * slots padded with -1; arrh/arrh0 are [R][3] (A in SI units, beta, Ea in
  * J/mol); rtype 0 elementary, 1 third-body, 2 Lindemann; rev 1 reversible via
- * K_c, 0 irreversible; eff_* is CSR over reactions (default efficiency 1);
- * nasa is [S][2][7] (low range first).  Returns NULL on bad sizes. */
+ * K_c, 0 irreversible, 2 reversible with the explicit reverse Arrhenius
+ * coefficients arrh_rev[R][3] (Sec. 3; may be NULL when no rev is 2); eff_*
+ * is CSR over reactions (default efficiency 1); nasa is [S][2][7] (low range
+ * first).  reactor 0: constant pressure, the per-reactor parameter p of the
+ * calls below is the pressure in Pa; reactor 1: constant volume (Sec. 3), the
+ * parameter is the fixed density in kg/m^3.  Returns NULL on bad input. */
 ora_mech* ora_mech_create(int32_t S, int32_t R, const double* mw, const double* nasa,
                           const double* tmid, const int32_t* reac, const int32_t* prod,
                           const double* arrh, const int32_t* rtype, const int32_t* rev,
                           const double* arrh0, const int32_t* eff_ptr, const int32_t* eff_sp,
-                          const double* eff_val);
+                          const double* eff_val, const double* arrh_rev, int32_t reactor);
 void ora_mech_free(ora_mech* m);
 
 /* NASA-7 properties of every species at T (Eq. tfits, read as the standard

@@ -20,5 +20,7 @@ from .draw import (  # noqa: F401
     draw_thermo_raw,
     draw_states,
     draw_efficiencies,
+    draw_densities,
+    pick_reactions,
 )
 from .configs import CONFIGS, load_mechanism, mechanism_path  # noqa: F401

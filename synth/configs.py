@@ -75,6 +75,16 @@ def reactor_states(cfg_name: str, n: int | None = None, seed_offset: int = 0):
                        cfg["t_range"], cfg["p_range_atm"])
 
 
+def cv_states(cfg_name: str, n: int, seed_offset: int = 0):
+    """Seeded constant-volume reactor states (y[n, S+1], rho[n]) for a named
+    workload's mechanism: compositions and T as in reactor_states, densities
+    log-uniform on [0.1, 3] kg/m^3 (seed state_seed + 7000 + seed_offset)."""
+    from .draw import draw_densities
+    y, _ = reactor_states(cfg_name, n=n, seed_offset=seed_offset)
+    rng = np.random.default_rng(CONFIGS[cfg_name]["state_seed"] + 7000 + seed_offset)
+    return y, draw_densities(rng, n)
+
+
 # Mixed workload: the three mechanisms in one batch (50/35/15 split of
 # 200000 reactors), T U[900, 2800] K, half the reactors of each mechanism
 # drawn from its near-ignition states, dt log-uniform on [1e-6, 1e-4] s.

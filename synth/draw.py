@@ -312,3 +312,17 @@ def draw_states(rng: np.random.Generator, names, elem, mw, elements, n: int,
     y[:, 0] = T
     y[:, 1:] = Y
     return y, p
+
+
+def draw_densities(rng: np.random.Generator, n: int, rho_range=(0.1, 3.0)) -> np.ndarray:
+    """Fixed densities of constant-volume reactors, log-uniform in kg/m^3
+    (0.1-3 kg/m^3 spans about 0.3-25 atm over 1000-2500 K)."""
+    lo, hi = np.log(rho_range[0]), np.log(rho_range[1])
+    return np.exp(rng.uniform(lo, hi, n))
+
+
+def pick_reactions(rng: np.random.Generator, rev: np.ndarray, frac: float) -> np.ndarray:
+    """A random subset (fraction frac) of the reversible reactions."""
+    idx = np.flatnonzero(np.asarray(rev) != 0)
+    k = int(round(frac * len(idx)))
+    return np.sort(rng.choice(idx, size=k, replace=False)) if k else np.zeros(0, int)

@@ -16,19 +16,23 @@ def _const_cp_nasa(S, a1=3.5, a6=-1000.0, a7=5.0):
     return nasa
 
 
-def linear_chain(k1: float, k2: float) -> dict:
+def linear_chain(k1: float, k2: float, a6=None) -> dict:
     """A -> B -> C, three isomers (same composition, same molar mass, same
-    constant-cp thermo), irreversible, beta = 0, Ea = 0.  With Y_A(0) = 1:
-    Y_A = exp(-k1 t), Y_B = k1/(k2-k1) (exp(-k1 t) - exp(-k2 t)), Y_C = 1 - Y_A - Y_B,
-    and T stays constant."""
+    constant cp/R = 3.5), irreversible, beta = 0, Ea = 0.  With Y_A(0) = 1:
+    Y_A = exp(-k1 t), Y_B = k1/(k2-k1) (exp(-k1 t) - exp(-k2 t)), Y_C = 1 - Y_A - Y_B.
+    a6 (optional, per species, K): the enthalpy offsets H_k/R = 3.5 T + a6_k;
+    equal offsets (the default) release no heat, so T stays constant."""
     S = 3
     elem = np.array([[1, 1], [1, 1], [1, 1]], np.int32)  # C1 O1 each
     mw = np.full(S, 28.010e-3)
     reac = np.array([[0, -1, -1], [1, -1, -1]], np.int32)
     prod = np.array([[1, -1, -1], [2, -1, -1]], np.int32)
     arrh = np.array([[k1, 0.0, 0.0], [k2, 0.0, 0.0]])
+    nasa = _const_cp_nasa(S)
+    if a6 is not None:
+        nasa[:, :, 5] = np.asarray(a6, float)[:, None]
     return dict(names=["A", "B", "C"], elements=["C", "O"], elem=elem, mw=mw,
-                nasa=_const_cp_nasa(S), tmid=np.full(S, 1000.0), reac=reac, prod=prod, arrh=arrh,
+                nasa=nasa, tmid=np.full(S, 1000.0), reac=reac, prod=prod, arrh=arrh,
                 rtype=np.zeros(2, np.uint8), rev=np.zeros(2, np.uint8), arrh0=np.zeros((2, 3)),
                 eff_ptr=np.zeros(3, np.int32), eff_sp=np.zeros(0, np.int32), eff_val=np.zeros(0))
 
