@@ -589,6 +589,76 @@ def run_fdjac(args):
     print(json.dumps(line), flush=True)
 
 
+def run_variants(args):
+    """The reactor and rate-form variants of Sec. 3 on the medium mechanism,
+    each timed like the default step (RHS x repeats, ROS4, RKF45 over
+    dt = 1e-5 s): constant pressure with K_c reverse rates (the default),
+    constant volume (densities log-uniform 0.1-3 kg/m^3), and constant
+    pressure with a quarter of the reversible reactions on explicit reverse
+    Arrhenius coefficients."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from oracle.mechgen import with_explicit_reverse
+    from synth.configs import CONFIGS, cv_states, load_mechanism, reactor_states
+    cfg = CONFIGS[WORKLOAD]
+    base = load_mechanism(cfg["mech"])
+    N = args.variant_reactors
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.float32, device="cuda")
+    res = {}
+    for name, mech, reactor in (("constant_pressure", base, 0), ("constant_volume", base, 1),
+                                ("explicit_reverse", with_explicit_reverse(base), 0)):
+        gm = ck.load_mechanism(mech, reactor=reactor)
+        work = ck.count_work(gm)
+        y_np, par_np = (cv_states(WORKLOAD, N) if reactor else reactor_states(WORKLOAD, n=N))
+        y0 = torch.as_tensor(y_np, device="cuda")
+        par = torch.as_tensor(par_np, device="cuda")
+        dt = torch.full((N,), cfg["dt"], dtype=torch.float64, device="cuda")
+        out = {}
+        f = torch.empty_like(y0)
+        t = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1.0)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            for _ in range(args.rhs_repeats_variant):
+                ck.rhs(gm, par, y0, f)
+            b.record()
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                t.append(a.elapsed_time(b) / 1e3 / args.rhs_repeats_variant)
+        trhs = float(np.mean(t))
+        out["rhs"] = {"evals_per_s": N / trhs,
+                      "tflops_dfma_eq": 2.0 * work["rhs_fp64"] * N / trhs / 1e12}
+        for mname, fn, per_key in (("ros4", ck.integrate_ros4, "ros4_step_fp64"),
+                                   ("rkf45", ck.integrate_rkf45, "rkf45_step_fp64")):
+            y = torch.empty_like(y0)
+            st = torch.empty(N, dtype=torch.int32, device="cuda")
+            steps = torch.empty((N, 2), dtype=torch.int32, device="cuda")
+            t = []
+            for i in range(args.warmup + args.steps):
+                flush.fill_(1.0)
+                y.copy_(y0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                fn(gm, par, y, dt, st, steps=steps)
+                b.record()
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    t.append(a.elapsed_time(b) / 1e3)
+            tm = float(np.mean(t))
+            att = float(steps.sum().item())
+            tf = 2.0 * work[per_key] * att / tm / 1e12
+            out[mname] = {"integrations_per_s": N / tm, "steps_mean": att / N, "tflops_dfma_eq": tf,
+                          "frac_of_fp64_peak": tf / FP64_PEAK_TFLOPS, "all_ok": bool((st == 0).all().item())}
+        res[name] = out
+    line = {"mode": "variants", "metric": "reactor integrations/s and RHS evals/s per reactor / rate-form variant",
+            "workload": f"medium: {len(base['mw'])} species / {len(base['rtype'])} reactions, {N} reactors, "
+                        f"dt={cfg['dt']:g} s, rtol 1e-9, atol 1e-12",
+            "results": res}
+    print(json.dumps(line), flush=True)
+
+
 def run_profile_case(args):
     """A small case of one kernel for ncu (warm-up launches, then 3 launches)."""
     import torch
@@ -630,7 +700,9 @@ def main():
                     help="profiling only: launch one kernel a few times on a small batch, print no bench line")
     ap.add_argument("--reactors", type=int, default=2048, help="batch size of --profile-case")
     ap.add_argument("--dt", type=float, default=None, help="dt of --profile-case (default: the workload's)")
-    ap.add_argument("--mode", choices=["bench", "serve", "batch", "fdjac"], default="bench")
+    ap.add_argument("--mode", choices=["bench", "serve", "batch", "fdjac", "variants"], default="bench")
+    ap.add_argument("--variant-reactors", type=int, default=32768, help="variants: medium-workload reactors")
+    ap.add_argument("--rhs-repeats-variant", type=int, default=20, help="variants: RHS passes per timing")
     ap.add_argument("--fd-reactors", type=int, default=8192, help="fdjac: medium-workload reactors")
     ap.add_argument("--batch-reactors", type=int, default=200000, help="batch: reactors of the mixed workload")
     ap.add_argument("--tune-sample", type=int, default=4096, help="batch: reactors timed per autotuner candidate")
@@ -644,6 +716,8 @@ def main():
         run_serve(args)
     elif args.mode == "fdjac":
         run_fdjac(args)
+    elif args.mode == "variants":
+        run_variants(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.profile_case:

@@ -81,7 +81,13 @@ typedef struct ck_mech ck_mech;
  * (c_i = P_r/(1+P_r), P_r = k0 [M]/k_inf with k0 from arrh0 and k_inf from
  * arrh).  [M] = sum_k eff_ik [X_k] with eff_ik from the CSR arrays
  * eff_ptr[R+1] / eff_sp / eff_val and 1 for unlisted species.  reversible:
- * 1 = k_r from K_c (Eqs. krev, kc), 0 = irreversible.  nasa[S][2][7] holds
+ * 1 = k_r from K_c (Eqs. krev, kc), 0 = irreversible, 2 = k_r from the
+ * explicit reverse Arrhenius coefficients arrh_rev[3i..3i+2] = (A_r, beta_r,
+ * Ea_r) (Sec. 3; arrh_rev may be NULL when no reaction uses it).  reactor
+ * selects the system the handle integrates (Sec. 3): 0 constant pressure,
+ * where the per-reactor parameter p of every call is the pressure in Pa; 1
+ * constant volume, where p is the reactor's fixed density in kg/m^3 and the
+ * temperature equation uses the internal energies u_k and c_v.  nasa[S][2][7] holds
  * the NASA-7 coefficients a1..a7 of the low (index 0, T < t_mid) and high
  * ranges (Eq. tfits).  elem_count[S][n_elements] (optional, may be NULL)
  * enables the atom-balance check; elem_mass[n_elements] (optional) enables
@@ -103,6 +109,8 @@ typedef struct {
   int32_t n_elements;
   const int32_t* elem_count;
   const double* elem_mass;
+  const double* arrh_rev;
+  int32_t reactor;
 } ck_mech_desc;
 
 /* Solver options.  The paper leaves the step-size controller unspecified

@@ -44,7 +44,8 @@ class MechDesc(C.Structure):
     _fields_ = [("n_species", C.c_int32), ("n_reactions", C.c_int32), ("mw", _DP), ("nasa", _DP),
                 ("t_mid", _DP), ("reac", _DP), ("prod", _DP), ("arrh", _DP), ("rtype", _DP),
                 ("reversible", _DP), ("arrh0", _DP), ("eff_ptr", _DP), ("eff_sp", _DP), ("eff_val", _DP),
-                ("n_elements", C.c_int32), ("elem_count", _DP), ("elem_mass", _DP)]
+                ("n_elements", C.c_int32), ("elem_count", _DP), ("elem_mass", _DP), ("arrh_rev", _DP),
+                ("reactor", C.c_int32)]
 
 
 class SolverOpts(C.Structure):
@@ -156,9 +157,14 @@ def _check_dtype(a, kind, name):
 
 
 class Mechanism:
-    """A mechanism loaded on the current CUDA device (see ck_load_mechanism)."""
+    """A mechanism loaded on the current CUDA device (see ck_load_mechanism).
 
-    def __init__(self, m: dict, check_atoms: bool = True):
+    reactor 0: constant pressure (the per-reactor parameter p of every call is
+    the pressure, Pa); 1: constant volume (p is the fixed density, kg/m^3).
+    Reactions with rev == 2 take explicit reverse Arrhenius coefficients from
+    m["arrh_rev"] [R, 3]."""
+
+    def __init__(self, m: dict, check_atoms: bool = True, reactor: int = 0):
         S = int(np.asarray(m["mw"]).shape[0])
         R = int(np.asarray(m["reac"]).shape[0])
         keep = dict(
@@ -175,6 +181,8 @@ class Mechanism:
             eff_sp=np.ascontiguousarray(m["eff_sp"], np.int32),
             eff_val=np.ascontiguousarray(m["eff_val"], np.float64),
         )
+        if "arrh_rev" in m:
+            keep["arrh_rev"] = np.ascontiguousarray(m["arrh_rev"], np.float64)
         n_el = 0
         if check_atoms and "elem" in m:
             keep["elem"] = np.ascontiguousarray(m["elem"], np.int32)
@@ -189,6 +197,8 @@ class Mechanism:
         d.n_elements = n_el
         d.elem_count = keep["elem"].ctypes.data if n_el else None
         d.elem_mass = None
+        d.arrh_rev = keep["arrh_rev"].ctypes.data if "arrh_rev" in keep and keep["arrh_rev"].size else None
+        d.reactor = int(reactor)
         h = C.c_void_p()
         _check(_lib.ck_load_mechanism(C.byref(d), C.byref(h)), "ck_load_mechanism")
         self.h = h
@@ -206,8 +216,8 @@ class Mechanism:
             pass
 
 
-def load_mechanism(m: dict, check_atoms: bool = True) -> Mechanism:
-    return Mechanism(m, check_atoms)
+def load_mechanism(m: dict, check_atoms: bool = True, reactor: int = 0) -> Mechanism:
+    return Mechanism(m, check_atoms, reactor)
 
 
 def rhs(mech: Mechanism, p, y, out, stream=None):

@@ -98,6 +98,8 @@ int validate(const ck_mech_desc* d) {
   if (S < 1 || S > CK_MAX_SPECIES) return fail(CK_ERANGE, "n_species must be in [1, 128]");
   if (R < 0 || R > CK_MAX_REACTIONS) return fail(CK_ERANGE, "n_reactions must be in [0, 32767]");
   if (!d->mw || !d->nasa || !d->t_mid) return fail(CK_EINVAL, "mw, nasa and t_mid are required");
+  if (d->reactor != 0 && d->reactor != 1)
+    return fail(CK_EINVAL, "reactor must be 0 (constant pressure) or 1 (constant volume)");
   if (R > 0 && (!d->reac || !d->prod || !d->arrh || !d->rtype || !d->reversible || !d->eff_ptr))
     return fail(CK_EINVAL, "reaction arrays are required when n_reactions > 0");
   for (int k = 0; k < S; ++k) {
@@ -128,8 +130,14 @@ int validate(const ck_mech_desc* d) {
       return fail(CK_EINVAL, "reaction " + std::to_string(i) + ": Arrhenius A must be positive and finite");
     const int t = d->rtype[i];
     if (t < 0 || t > 2) return fail(CK_EINVAL, "reaction " + std::to_string(i) + ": rtype must be 0, 1 or 2");
-    if (d->reversible[i] != 0 && d->reversible[i] != 1)
-      return fail(CK_EINVAL, "reaction " + std::to_string(i) + ": reversible must be 0 or 1");
+    if (d->reversible[i] < 0 || d->reversible[i] > 2)
+      return fail(CK_EINVAL, "reaction " + std::to_string(i) + ": reversible must be 0, 1 or 2");
+    if (d->reversible[i] == 2) {
+      if (!d->arrh_rev) return fail(CK_EINVAL, "arrh_rev is required for explicit reverse rates");
+      const double* ar = d->arrh_rev + i * 3;
+      if (!(ar[0] > 0.0) || !finite(ar[0]) || !finite(ar[1]) || !finite(ar[2]))
+        return fail(CK_EINVAL, "reaction " + std::to_string(i) + ": reverse A must be positive and finite");
+    }
     if (t == 2) {
       if (!d->arrh0) return fail(CK_EINVAL, "arrh0 is required for fall-off reactions");
       const double* a0 = d->arrh0 + i * 3;
@@ -201,12 +209,12 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
     return c;
   };
   auto key = [&](int i) {
-    return ((d->rtype[i] * 2 + d->reversible[i]) * 4 + nside(d->reac, i)) * 4 + nside(d->prod, i);
+    return ((d->rtype[i] * 3 + d->reversible[i]) * 4 + nside(d->reac, i)) * 4 + nside(d->prod, i);
   };
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return key(a) < key(b); });
   std::vector<RxnRec> rx(R);
   std::vector<int16_t> eff_sp;
-  std::vector<double> eff_m1;
+  std::vector<double> eff_m1, revp;
   for (int ii = 0; ii < R; ++ii) {
     const int i = order[ii];
     RxnRec& r = rx[ii];
@@ -217,6 +225,13 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
     r.EoR2 = (double)((long double)a[2] / (Rg * ln2));
     r.type = (int8_t)d->rtype[i];
     r.rev = (int8_t)d->reversible[i];
+    if (r.rev == 2) {
+      const double* ar = d->arrh_rev + i * 3;
+      r.rev_ix = (int16_t)(revp.size() / 3);
+      revp.push_back((double)std::log2((long double)ar[0]));
+      revp.push_back(ar[1]);
+      revp.push_back((double)((long double)ar[2] / (Rg * ln2)));
+    }
     if (r.type == 2) {
       const double* a0 = d->arrh0 + i * 3;
       r.lA02 = (double)(std::log2((long double)a0[0]));
@@ -351,6 +366,7 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   L.invW = place(sizeof(double) * S);
   L.eff_sp = place(sizeof(int16_t) * eff_sp.size());
   L.eff_m1 = place(sizeof(double) * eff_m1.size());
+  L.revp = place(sizeof(double) * revp.size());
   L.tab = place(sizeof(double) * 256);
   L.bytes = (uint32_t)off;
   const size_t off_csr_ptr = place(sizeof(int32_t) * (S + 1));
@@ -375,6 +391,7 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   put(L.invW, invW.data(), sizeof(double) * S);
   put(L.eff_sp, eff_sp.data(), sizeof(int16_t) * eff_sp.size());
   put(L.eff_m1, eff_m1.data(), sizeof(double) * eff_m1.size());
+  put(L.revp, revp.data(), sizeof(double) * revp.size());
   put(L.tab, tab.data(), sizeof(double) * 256);
   put(off_csr_ptr, csr_ptr.data(), sizeof(int32_t) * (S + 1));
   put(off_csr_rx, csr_rx.data(), sizeof(int32_t) * csr_rx.size());
@@ -418,6 +435,8 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   dm.csr_nnz = (int)csr_rx.size();
   dm.rxn = reinterpret_cast<const RxnRec*>(b + L.rx);
   dm.thermo = reinterpret_cast<const double*>(b + L.th);
+  dm.revp = reinterpret_cast<const double*>(b + L.revp);
+  dm.cv = d->reactor;
   dm.tmid = reinterpret_cast<const double*>(b + L.tmid);
   dm.W = reinterpret_cast<const double*>(b + L.W);
   dm.invW = reinterpret_cast<const double*>(b + L.invW);
@@ -665,7 +684,8 @@ double rhs_count(const ck::HostMech& hm) {
   double c = 20.0 + 24.0 * hm.S;
   for (const auto& r : hm.rx) {
     c += 2 + 8 + (r.nreac - 1) + 1 + (r.nreac + r.nprod);
-    if (r.rev) c += 1 + (r.nreac + r.nprod) + 1 + 8 + (r.nprod - 1) + 1;
+    if (r.rev == 1) c += 1 + (r.nreac + r.nprod) + 1 + 8 + (r.nprod - 1) + 1;
+    if (r.rev == 2) c += 2 + 8 + (r.nprod - 1) + 1;
     if (r.type) c += r.eff_cnt + 1;
     if (r.type == 2) c += 2 + 1 + 8 + 1 + 1 + 1 + 1;
   }
@@ -683,7 +703,8 @@ double jac_count(const ck::HostMech& hm) {
   double c = 4.0 * S + S * S + 3.0 * S * S + 12.0 * S + 30.0;
   for (const auto& r : hm.rx) {
     double per = 3 + 3 + 4 + 1 + 6 + 1;  // dlnkf, c k, w, D, dq/dT
-    if (r.rev) per += (r.nreac + r.nprod) + 2;
+    if (r.rev == 1) per += (r.nreac + r.nprod) + 2;
+    if (r.rev == 2) per += 2;
     if (r.type == 2) per += 7;
     per += (r.nreac == 2 ? 2 : (r.nreac == 3 ? 6 : 0));
     if (r.rev) per += (r.nprod == 2 ? 2 : (r.nprod == 3 ? 6 : 1));

@@ -35,11 +35,11 @@ struct __align__(16) RxnRec {
   double nprod_d;  // product count, as FP64
   int16_t sp[6];    // reactant slots 0..2, product slots 3..5, -1 padded
   int8_t type;      // 0 elementary, 1 third-body, 2 Lindemann
-  int8_t rev;       // 1 reversible through K_c
+  int8_t rev;       // 1 reversible through K_c, 2 explicit reverse Arrhenius
   int8_t dnu;
   int8_t nreac, nprod, pad0;
   int16_t eff_beg, eff_cnt;  // slice of the efficiency table (eff - 1 != 0)
-  int16_t pad1;
+  int16_t rev_ix;            // rev == 2: row of the explicit reverse table
 };
 static_assert(sizeof(RxnRec) == 96, "RxnRec layout");
 
@@ -61,6 +61,7 @@ struct DevMech {
   int n_eff;              // entries of the efficiency table
   int csr_nnz;            // entries of the species -> reaction table
   int all_same_tmid;      // every species shares one T_mid
+  int cv;                 // 1: constant volume (the parameter is rho), 0: constant pressure
   double tmid0;
   const RxnRec* rxn;      // [R]
   const double* thermo;   // [S][2][TH_STRIDE]
@@ -73,6 +74,7 @@ struct DevMech {
   const int32_t* csr_rx;  // [csr_nnz] reaction index
   const double* csr_nu;   // [csr_nnz] net stoichiometric coefficient
   const double* tab;      // [256] 2^(j/256)
+  const double* revp;     // [n_rev][3] explicit reverse: log2 A_r, beta_r, Ea_r / (R ln 2)
   // Team kernels walk the reactions in chunks of `chunk` (= CTA size).
   // csr_cptr[k (n_chunks + 1) + c] = first CSR entry of species k whose
   // reaction lies in chunk c or later.  Jacobian assembly, chunk c: the

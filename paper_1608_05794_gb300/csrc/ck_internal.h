@@ -14,7 +14,7 @@ namespace ck {
 // Byte offsets of the sections of the staged table block (all 16-byte
 // aligned).  The block is [rxn | thermo | tmid | W | invW | eff_sp | eff_m1 | exp2].
 struct StageLayout {
-  uint32_t rx, th, tmid, W, invW, eff_sp, eff_m1, tab, bytes;
+  uint32_t rx, th, tmid, W, invW, eff_sp, eff_m1, revp, tab, bytes;
 };
 
 struct HostMech {

@@ -77,6 +77,8 @@ __device__ __forceinline__ MechView view_of(const DevMech& d, const StageLayout&
   m.eff_sp = reinterpret_cast<const int16_t*>(base + L.eff_sp);
   m.eff_m1 = reinterpret_cast<const double*>(base + L.eff_m1);
   m.tab = reinterpret_cast<const double*>(base + L.tab);
+  m.revp = reinterpret_cast<const double*>(base + L.revp);
+  m.cv = d.cv;
   return m;
 }
 

@@ -65,7 +65,7 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
   for (int k = threadIdx.x; k < S; k += blockDim.x) s = fma(y[1 + k], m.invW[k], s);
   const double sumYW = team_sum(s, b.red);
   x.Wbar = 1.0 / sumYW;
-  x.rho = p / (R_GAS * x.T * sumYW);
+  x.rho = m.cv ? p : p / (R_GAS * x.T * sumYW);  // constant volume: p is the density
   double c = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const double xk = x.rho * (y[1 + k] * m.invW[k]);
@@ -103,7 +103,19 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
   if (r.nreac > 1) fwd *= X[r.sp[1]];
   if (r.nreac > 2) fwd *= X[r.sp[2]];
   double kr = 0.0, rv = 0.0, dlnkc = 0.0;
-  if (r.rev) {
+  if (r.rev == 2) {
+    // explicit reverse Arrhenius; for the Jacobian, d ln k_r/dT enters as
+    // d ln k_f/dT - d ln K_c/dT, so dlnkc carries their difference
+    const double* ra = m.revp + 3 * r.rev_ix;
+    kr = ck_exp2(fma(-ra[2], x.invT, fma(ra[1], x.log2T, ra[0])), tab);
+    rv = X[r.sp[3]];
+    if (r.nprod > 1) rv *= X[r.sp[4]];
+    if (r.nprod > 2) rv *= X[r.sp[5]];
+    if (want_jac) {
+      const double dlnkf = fma(r.EoR2 * LN2, x.invT, r.beta) * x.invT;
+      dlnkc = dlnkf - fma(ra[2] * LN2, x.invT, ra[1]) * x.invT;
+    }
+  } else if (r.rev) {
     double l2kc = r.dnu_d * (LOG2_P0_OVER_R - x.log2T);
     l2kc += g2[r.sp[3]];
     if (r.nprod > 1) l2kc += g2[r.sp[4]];
@@ -189,9 +201,10 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
     // products (homogeneous of degree nreac / nprod) plus the [M] part.
     const double D = fma(ckf * fwd, r.nreac_d, -(ckr * rv) * r.nprod_d) + M * w;
     b.D[i] = D;
-    // dq/dT at fixed [X], then the total derivative at fixed Y (d[X]/dT = -[X]/T)
+    // dq/dT at fixed [X], then the total derivative at fixed Y (d[X]/dT =
+    // -[X]/T at constant pressure, 0 at constant volume)
     const double dqTX = fma(dcdT, net, ckf * fwd * dlnkf - ckr * rv * (dlnkf - dlnkc));
-    b.dqT[i] = fma(-D, x.invT, dqTX);
+    b.dqT[i] = m.cv ? dqTX : fma(-D, x.invT, dqTX);
   }
 }
 
@@ -216,11 +229,12 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
     team_sync();
   }
   const double invrho = 1.0 / x.rho;
+  const double cvf = m.cv ? 1.0 : 0.0;  // constant volume: U/RT = H/RT - 1, cv/R = cp/R - 1
   double cpm = 0.0, hw = 0.0;
   for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
     const double w = b.wd[k];
-    cpm = fma(y[1 + k] * m.invW[k], b.cpR[k], cpm);
-    hw = fma(b.hRT[k], w, hw);
+    cpm = fma(y[1 + k] * m.invW[k], b.cpR[k] - cvf, cpm);
+    hw = fma(b.hRT[k] - cvf, w, hw);
     f[1 + k] = w * (m.W[k] * invrho);
   }
   cpm = team_sum(cpm, b.red);
@@ -240,7 +254,12 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
 //   J[0][1+j]   = -(T (rho cs_j - Wbar HE)/(rho cpm) + Tdot (cp_j/cpm - Wbar)) / W_j,
 //   J[0][0]     = -(sum cp_k wdot_k + T sum H_k/RT a_k)/(rho cpm) - Tdot (dcpm/cpm - 1/T),
 // with cs_j = sum_k H_k/RT (A_kj + u_k), HE = sum_k H_k/RT E_k, and heat
-// capacities in units of R.
+// capacities in units of R.  Constant volume (rho fixed; u_k, c_v in Eq.
+// tdot): the Wbar and 1/T terms vanish, a_k is taken at fixed [X], and H/RT,
+// cp/R become U/RT = H/RT - 1 and cv/R = cp/R - 1:
+//   J[1+k][1+j] = W_k (A_kj + u_k) / W_j,   J[1+k][0] = W_k a_k / rho,
+//   J[0][1+j]   = -(T cs_j / cvm + Tdot cv_j / cvm) / W_j,
+//   J[0][0]     = -(sum cv_k wdot_k + T sum U_k/RT a_k)/(rho cvm) - Tdot dcpm/cvm.
 static __device__ void team_jacobian(const DevMech& m, const double* tab, double p, const double* y,
                               double* f, double* J, TeamBufs& b, Mix& x) {
   const int S = m.S, n = m.n;
@@ -283,22 +302,27 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
     }
     team_sync();
   }
-  // column sums for the temperature row, and the RHS itself
+  // column sums for the temperature row, and the RHS itself.  Constant
+  // volume: rho is fixed, so every term that comes from d rho/dT or
+  // d rho/dY (cpf) drops out, and U/RT = H/RT - 1, cv/R = cp/R - 1 take the
+  // places of H/RT and cp/R (cvf)
   const double invrho = 1.0 / x.rho;
+  const double cvf = m.cv ? 1.0 : 0.0, cpf = 1.0 - cvf;
   double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = 0.0, cw = 0.0, ha = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const double yk = y[1 + k] * m.invW[k];
-    cpm = fma(yk, b.cpR[k], cpm);
+    const double e = b.hRT[k] - cvf, c = b.cpR[k] - cvf;
+    cpm = fma(yk, c, cpm);
     dcpm = fma(yk, b.dcpR[k], dcpm);
-    hw = fma(b.hRT[k], b.wd[k], hw);
+    hw = fma(e, b.wd[k], hw);
     he = fma(b.hRT[k], b.E[k], he);
-    cw = fma(b.cpR[k], b.wd[k], cw);
-    ha = fma(b.hRT[k], b.aT[k], ha);
+    cw = fma(c, b.wd[k], cw);
+    ha = fma(e, b.aT[k], ha);
     f[1 + k] = b.wd[k] * (m.W[k] * invrho);
   }
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
     double s = 0.0;
-    for (int k = 0; k < S; ++k) s = fma(b.hRT[k], J[(size_t)(1 + k) * n + 1 + j] + b.u[k], s);
+    for (int k = 0; k < S; ++k) s = fma(b.hRT[k] - cvf, J[(size_t)(1 + k) * n + 1 + j] + b.u[k], s);
     b.cs[j] = s;
   }
   cpm = team_sum(cpm, b.red);
@@ -314,19 +338,19 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   for (int e = threadIdx.x; e < SS; e += blockDim.x) {
     const int k = e / S, j = e - k * S;
     double* a = J + (size_t)(1 + k) * n + 1 + j;
-    const double ck = m.W[k] * x.Wbar * (b.wd[k] - b.E[k]) * invrho;
+    const double ck = cpf * m.W[k] * x.Wbar * (b.wd[k] - b.E[k]) * invrho;
     *a = fma(m.W[k], *a + b.u[k], ck) * m.invW[j];
   }
   for (int k = threadIdx.x; k < S; k += blockDim.x)
-    J[(size_t)(1 + k) * n] = m.W[k] * invrho * fma(b.wd[k], x.invT, b.aT[k]);
+    J[(size_t)(1 + k) * n] = m.W[k] * invrho * fma(cpf * b.wd[k], x.invT, b.aT[k]);
   const double inv_rc = 1.0 / (x.rho * cpm);
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
-    const double t1 = x.T * (x.rho * b.cs[j] - x.Wbar * he) * inv_rc;
-    const double t2 = Tdot * (b.cpR[j] / cpm - x.Wbar);
+    const double t1 = x.T * (x.rho * b.cs[j] - cpf * x.Wbar * he) * inv_rc;
+    const double t2 = Tdot * ((b.cpR[j] - cvf) / cpm - cpf * x.Wbar);
     J[1 + j] = -(t1 + t2) * m.invW[j];
   }
   if (threadIdx.x == 0) {
-    J[0] = -fma(x.T, ha, cw) * inv_rc - Tdot * (dcpm / cpm - x.invT);
+    J[0] = -fma(x.T, ha, cw) * inv_rc - Tdot * (dcpm / cpm - cpf * x.invT);
     f[0] = Tdot;
   }
   team_sync();

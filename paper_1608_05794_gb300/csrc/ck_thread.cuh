@@ -18,6 +18,8 @@ struct MechView {
   const int16_t* eff_sp;
   const double* eff_m1;
   const double* tab;  // 2^(j/256), j = 0..255
+  const double* revp; // explicit reverse rows: log2 A_r, beta_r, Ea_r / (R ln 2)
+  int cv;             // 1: constant volume (p is the density)
 };
 
 // f = (dT/dt, dY_k/dt) at state y (Eqs. ydot, tdot, wdot, kfor, krev, kc,
@@ -29,6 +31,9 @@ struct MechView {
 //   c = 1, [M], or P_r/(1+P_r) with P_r = 2^(log2 k0 - log2 k_inf) [M],
 //   q = c (k_f prod [X]^nu' - k_r prod [X]^nu''),  wdot_k = sum (nu'' - nu') q,
 //   dY_k/dt = wdot_k W_k / rho, dT/dt = -T sum_k (H_k/RT) wdot_k / (rho sum_k Y_k (cp_k/R)/W_k).
+// Explicit reverse rows: k_r = 2^(log2 A_r + beta_r log2 T - Ea_r/(R T ln 2)).
+// Constant volume (Sec. 3): rho = p (the parameter is the density) and
+// H/RT -> U/RT = H/RT - 1, cp/R -> cv/R = cp/R - 1 in dT/dt.
 __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const double* y, int ys,
                                            double* f, int fs, double* X, double* g2, double* wd) {
   const int S = m.S;
@@ -39,7 +44,7 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
   const double T2 = T * T, T3 = T2 * T, T4 = T3 * T;
   double sumYW = 0.0;
   for (int k = 0; k < S; ++k) sumYW = fma(y[(1 + k) * ys], m.invW[k], sumYW);
-  const double rho = p / (R_GAS * T * sumYW);
+  const double rho = m.cv ? p : p / (R_GAS * T * sumYW);
   double Ctot = 0.0;
   for (int k = 0; k < S; ++k) {
     const double xk = rho * (y[(1 + k) * ys] * m.invW[k]);
@@ -63,7 +68,14 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
     if (r.nreac > 1) fwd *= X[r.sp[1]];
     if (r.nreac > 2) fwd *= X[r.sp[2]];
     double net = kf * fwd;
-    if (r.rev) {
+    if (r.rev == 2) {
+      const double* ra = m.revp + 3 * r.rev_ix;
+      const double kr = ck_exp2(fma(-ra[2], invT, fma(ra[1], log2T, ra[0])), m.tab);
+      double rv = X[r.sp[3]];
+      if (r.nprod > 1) rv *= X[r.sp[4]];
+      if (r.nprod > 2) rv *= X[r.sp[5]];
+      net = fma(-kr, rv, net);
+    } else if (r.rev) {
       double l2kc = r.dnu_d * lp2;
       l2kc += g2[r.sp[3]];
       if (r.nprod > 1) l2kc += g2[r.sp[4]];
@@ -97,11 +109,12 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
     if (r.nprod > 2) wd[r.sp[5]] += q;
   }
   const double invrho = 1.0 / rho;
+  const double cvf = m.cv ? 1.0 : 0.0;
   double cpm = 0.0, hw = 0.0;
   for (int k = 0; k < S; ++k) {
     const double* a = m.th + k * TH_PER_SPECIES + (T < m.tmid[k] ? 0 : TH_STRIDE);
-    double cp = fma(a[4], T4, fma(a[3], T3, fma(a[2], T2, fma(a[1], T, a[0]))));
-    double h = fma(a[10], invT, fma(a[9], T4, fma(a[8], T3, fma(a[7], T2, fma(a[6], T, a[5])))));
+    double cp = fma(a[4], T4, fma(a[3], T3, fma(a[2], T2, fma(a[1], T, a[0])))) - cvf;
+    double h = fma(a[10], invT, fma(a[9], T4, fma(a[8], T3, fma(a[7], T2, fma(a[6], T, a[5]))))) - cvf;
     const double w = wd[k];
     cpm = fma(y[(1 + k) * ys] * m.invW[k], cp, cpm);
     hw = fma(h, w, hw);
