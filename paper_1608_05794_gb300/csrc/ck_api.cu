@@ -325,12 +325,16 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
         const int li = i - c * chunk;
         const double nu = csr_nu[e];
         const RxnRec& r = rx[i];
-        for (int s2 = 0; s2 < r.nreac; ++s2) ent[(size_t)k * S + r.sp[s2]].push_back({nu, li * JP + s2});
+        // coefficients carry W_k / W_j, the factor of the species block
+        // dY_k/dY_j (so the assembly needs no per-entry rescaling)
+        auto wr = [&](int j) { return (double)((long double)W[k] / (long double)W[j]); };
+        for (int s2 = 0; s2 < r.nreac; ++s2)
+          ent[(size_t)k * S + r.sp[s2]].push_back({nu * wr(r.sp[s2]), li * JP + s2});
         if (r.rev)
           for (int s2 = 0; s2 < r.nprod; ++s2)
-            ent[(size_t)k * S + r.sp[3 + s2]].push_back({nu, li * JP + 3 + s2});
+            ent[(size_t)k * S + r.sp[3 + s2]].push_back({nu * wr(r.sp[3 + s2]), li * JP + 3 + s2});
         for (int q = r.eff_beg; q < r.eff_beg + r.eff_cnt; ++q)
-          ent[(size_t)k * S + eff_sp[q]].push_back({nu * eff_m1[q], li * JP + 6});
+          ent[(size_t)k * S + eff_sp[q]].push_back({nu * eff_m1[q] * wr(eff_sp[q]), li * JP + 6});
       }
     }
     std::vector<int> order_e;
@@ -699,8 +703,8 @@ double rhs_exps(const ck::HostMech& hm) {
 double jac_count(const ck::HostMech& hm) {
   const double S = hm.S;
   // species pass extras (dcp), the species-block zeroing is not FP64,
-  // column sums S^2, transform 3 S^2, temperature row / column 12 S, J00
-  double c = 4.0 * S + S * S + 3.0 * S * S + 12.0 * S + 30.0;
+  // column sums S^2, dense row terms S^2, temperature row / column 14 S, J00
+  double c = 4.0 * S + S * S + S * S + 14.0 * S + 30.0;
   for (const auto& r : hm.rx) {
     double per = 3 + 3 + 4 + 1 + 6 + 1;  // dlnkf, c k, w, D, dq/dT
     if (r.rev == 1) per += (r.nreac + r.nprod) + 2;

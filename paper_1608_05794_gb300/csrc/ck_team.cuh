@@ -305,10 +305,11 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   // column sums for the temperature row, and the RHS itself.  Constant
   // volume: rho is fixed, so every term that comes from d rho/dT or
   // d rho/dY (cpf) drops out, and U/RT = H/RT - 1, cv/R = cp/R - 1 take the
-  // places of H/RT and cp/R (cvf)
+  // places of H/RT and cp/R (cvf).  The contributions were pre-scaled by
+  // W_k/W_j, so J holds A'_kj = W_k A_kj / W_j here.
   const double invrho = 1.0 / x.rho;
   const double cvf = m.cv ? 1.0 : 0.0, cpf = 1.0 - cvf;
-  double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = 0.0, cw = 0.0, ha = 0.0;
+  double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = 0.0, cw = 0.0, ha = 0.0, eu = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const double yk = y[1 + k] * m.invW[k];
     const double e = b.hRT[k] - cvf, c = b.cpR[k] - cvf;
@@ -318,12 +319,12 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
     he = fma(b.hRT[k], b.E[k], he);
     cw = fma(c, b.wd[k], cw);
     ha = fma(e, b.aT[k], ha);
+    eu = fma(e, b.u[k], eu);
     f[1 + k] = b.wd[k] * (m.W[k] * invrho);
-  }
-  for (int j = threadIdx.x; j < S; j += blockDim.x) {
-    double s = 0.0;
-    for (int k = 0; k < S; ++k) s = fma(b.hRT[k] - cvf, J[(size_t)(1 + k) * n + 1 + j] + b.u[k], s);
-    b.cs[j] = s;
+    // per row: e_k / W_k for the column sums, and the dense part of the
+    // species block, W_k u_k + W_k Wbar (wdot_k - E_k) / rho (constant p)
+    b.hRT[k] = e * m.invW[k];
+    b.u[k] = m.W[k] * fma(cpf * x.Wbar * invrho, b.wd[k] - b.E[k], b.u[k]);
   }
   cpm = team_sum(cpm, b.red);
   dcpm = team_sum(dcpm, b.red);
@@ -331,26 +332,33 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   he = team_sum(he, b.red);
   cw = team_sum(cw, b.red);
   ha = team_sum(ha, b.red);
+  eu = team_sum(eu, b.red);
   const double Tdot = -x.T * hw / (x.rho * cpm);
+  // cs_j = sum_k e_k (A_kj + u_k) = W_j sum_k (e_k / W_k) A'_kj + sum_k e_k u_k
+  for (int j = threadIdx.x; j < S; j += blockDim.x) {
+    double s = 0.0;
+    for (int k = 0; k < S; ++k) s = fma(b.hRT[k], J[(size_t)(1 + k) * n + 1 + j], s);
+    b.cs[j] = fma(m.W[j], s, eu);
+  }
   team_sync();
-  // species block and temperature column
+  // species block (J_kj = A'_kj + dense_k / W_j) and temperature column
   const int SS = S * S;
   for (int e = threadIdx.x; e < SS; e += blockDim.x) {
     const int k = e / S, j = e - k * S;
     double* a = J + (size_t)(1 + k) * n + 1 + j;
-    const double ck = cpf * m.W[k] * x.Wbar * (b.wd[k] - b.E[k]) * invrho;
-    *a = fma(m.W[k], *a + b.u[k], ck) * m.invW[j];
+    *a = fma(b.u[k], m.invW[j], *a);
   }
   for (int k = threadIdx.x; k < S; k += blockDim.x)
     J[(size_t)(1 + k) * n] = m.W[k] * invrho * fma(cpf * b.wd[k], x.invT, b.aT[k]);
-  const double inv_rc = 1.0 / (x.rho * cpm);
+  const double inv_cpm = 1.0 / cpm;
+  const double inv_rc = invrho * inv_cpm;
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
     const double t1 = x.T * (x.rho * b.cs[j] - cpf * x.Wbar * he) * inv_rc;
-    const double t2 = Tdot * ((b.cpR[j] - cvf) / cpm - cpf * x.Wbar);
+    const double t2 = Tdot * fma(b.cpR[j] - cvf, inv_cpm, -cpf * x.Wbar);
     J[1 + j] = -(t1 + t2) * m.invW[j];
   }
   if (threadIdx.x == 0) {
-    J[0] = -fma(x.T, ha, cw) * inv_rc - Tdot * (dcpm / cpm - cpf * x.invT);
+    J[0] = -fma(x.T, ha, cw) * inv_rc - Tdot * fma(dcpm, inv_cpm, -cpf * x.invT);
     f[0] = Tdot;
   }
   team_sync();
