@@ -685,10 +685,13 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
 
 // FP64 instruction counts of this library's formulation (see ck.h).
 double rhs_count(const ck::HostMech& hm) {
-  double c = 20.0 + 24.0 * hm.S;
+  // species pass: mixture, NASA-7 polynomials and the two Gibbs factors
+  // 2^(+-g_k) (8 each) per species
+  double c = 20.0 + 40.0 * hm.S;
   for (const auto& r : hm.rx) {
     c += 2 + 8 + (r.nreac - 1) + 1 + (r.nreac + r.nprod);
-    if (r.rev == 1) c += 1 + (r.nreac + r.nprod) + 1 + 8 + (r.nprod - 1) + 1;
+    // 1/K_c as a product of species factors, then k_r and the reverse product
+    if (r.rev == 1) c += 1 + (r.nreac + r.nprod) + 1 + (r.nprod - 1) + 1;
     if (r.rev == 2) c += 2 + 8 + (r.nprod - 1) + 1;
     if (r.type) c += r.eff_cnt + 1;
     if (r.type == 2) c += 2 + 1 + 8 + 1 + 1 + 1 + 1;
@@ -696,8 +699,8 @@ double rhs_count(const ck::HostMech& hm) {
   return c;
 }
 double rhs_exps(const ck::HostMech& hm) {
-  double c = 0.0;
-  for (const auto& r : hm.rx) c += 1 + (r.rev ? 1 : 0) + (r.type == 2 ? 1 : 0);
+  double c = 2.0 * hm.S;  // 2^(+-g_k) per species
+  for (const auto& r : hm.rx) c += 1 + (r.rev == 2 ? 1 : 0) + (r.type == 2 ? 1 : 0);
   return c;
 }
 double jac_count(const ck::HostMech& hm) {

@@ -18,6 +18,8 @@ constexpr double P_STD = 101325.0;          // p0 of Eq. kc, Pa
 constexpr double LN2 = 0.6931471805599453094;
 constexpr double INV_LN2 = 1.4426950408889634074;
 constexpr double LOG2_P0_OVER_R = 13.573007627848395117;  // log2(101325 / 8.314462618)
+constexpr double R_OVER_P0 = R_GAS / P_STD;               // R T / p0 is the molar volume at p0, m^3/mol
+constexpr double P0_OVER_R = P_STD / R_GAS;
 
 // One reaction, 96 bytes, read uniformly by all lanes (thread-per-reactor
 // kernels) or by one lane per reaction (team kernels).  The loader sorts the
@@ -121,6 +123,14 @@ __device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ t
   double res = fma(tj, q, tj);
   long long b = __double_as_longlong(res) + ((long long)e << 52);
   return __longlong_as_double(b);
+}
+
+// (R T / p0)^dnu for dnu = nprod - nreac in [-2, 2]: the concentration
+// factor of 1/K_c (Eq. kc), by multiplication instead of an exponential.
+__device__ __forceinline__ double rt_over_p0_pow(int dnu, double T, double invT) {
+  const double q = dnu >= 0 ? T * R_OVER_P0 : invT * P0_OVER_R;
+  const int a = dnu >= 0 ? dnu : -dnu;
+  return a == 0 ? 1.0 : (a == 1 ? q : q * q);
 }
 
 // ---------------------------------------------------------------- statuses

@@ -18,15 +18,15 @@ __host__ __device__ __forceinline__ int team_bufs_doubles(int S, int chunk) { re
 __device__ __forceinline__ TeamBufs carve_bufs(double* base, int S, int CH) {
   TeamBufs b;
   b.X = base;
-  b.g2 = b.X + S;
-  b.hRT = b.g2 + S;
+  b.Gp = b.X + S;
+  b.hRT = b.Gp + S;
   b.cpR = b.hRT + S;
-  b.dcpR = b.cpR + S;
-  b.wd = b.dcpR + S;
+  b.Gm = b.cpR + S;
+  b.wd = b.Gm + S;
   b.aT = b.wd + S;
   b.E = b.aT + S;
   b.u = b.E + S;
-  b.cs = b.g2;  // column sums reuse g2 (free after the reaction passes)
+  b.cs = b.Gp;  // column sums reuse Gp (free after the reaction passes)
   b.q = b.u + S;
   b.dqT = b.q + CH;
   b.D = b.dqT + CH;

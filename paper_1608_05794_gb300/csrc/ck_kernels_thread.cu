@@ -98,7 +98,7 @@ __global__ void __launch_bounds__(128) k_rhs(DevMech d, StageLayout L, int stage
     base = smem + STAGE_HDR;
   }
   const MechView m = view_of(d, L, base);
-  double X[MAXS], g2[MAXS], wd[MAXS];
+  double X[MAXS], g2[2 * MAXS], wd[MAXS];
   const int n = d.n;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
        r += (int64_t)gridDim.x * blockDim.x) {
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) k_rkf45(DevMech d, StageLayout L, int sta
   }
   const MechView m = view_of(d, L, base);
   constexpr int MAXN = MAXS + 1;
-  double X[MAXS], g2[MAXS], wd[MAXS];
+  double X[MAXS], g2[2 * MAXS], wd[MAXS];
   double yv[MAXN], yt[MAXN], k[6][MAXN];
   const int n = d.n;
   const bool fixed = sp.fixed_h > 0.0;

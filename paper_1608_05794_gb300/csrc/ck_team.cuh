@@ -36,10 +36,11 @@ __device__ __forceinline__ void team_sync() {
 
 // Shared-memory work arrays of one team.
 // Reactions are processed in chunks of m.chunk (the CTA size), so the
-// per-reaction arrays hold one chunk; cs aliases g2 (free once the reaction
-// passes are done).
+// per-reaction arrays hold one chunk; cs aliases Gp (free once the reaction
+// passes are done).  Gp_k = 2^(g_k) and Gm_k = 2^(-g_k) with g_k = (S/R -
+// H/RT)_k / ln 2, so that 1/K_c of Eq. kc is a product of species factors.
 struct TeamBufs {
-  double *X, *g2, *hRT, *cpR, *dcpR, *wd, *aT, *E, *u, *cs;  // [S]
+  double *X, *Gp, *hRT, *cpR, *Gm, *wd, *aT, *E, *u, *cs;  // [S]
   double *q, *dqT, *D;                                        // [chunk]
   double* P;                                                  // [chunk * JP] Jacobian partials
   double* red;                                                // [48]
@@ -48,11 +49,12 @@ struct TeamBufs {
 // Mixture quantities shared by the RHS and the Jacobian.
 struct Mix {
   double T, invT, lnT, log2T, T2, T3, T4, rho, Wbar, Ctot;
+  double dcpm;  // this thread's part of sum_k Y_k/W_k d(cp_k/R)/dT (Jacobian only)
 };
 
 // Species pass: rho, [X_k], Gibbs / enthalpy / heat-capacity polynomials.
 __device__ __forceinline__ void team_species(const DevMech& m, double p, const double* y,
-                                             TeamBufs& b, Mix& x, bool want_dcp) {
+                                             TeamBufs& b, Mix& x, bool want_dcp, const double* tab) {
   const int S = m.S;
   x.T = y[0];
   x.invT = 1.0 / x.T;
@@ -66,7 +68,7 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
   const double sumYW = team_sum(s, b.red);
   x.Wbar = 1.0 / sumYW;
   x.rho = m.cv ? p : p / (R_GAS * x.T * sumYW);  // constant volume: p is the density
-  double c = 0.0;
+  double c = 0.0, dcpm = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const double xk = x.rho * (y[1 + k] * m.invW[k]);
     b.X[k] = xk;
@@ -77,15 +79,19 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
     g = fma(a[14], x.T2, g);
     g = fma(a[15], x.T3, g);
     g = fma(a[16], x.T4, g);
-    b.g2[k] = fma(a[17], x.invT, g);
+    g = fma(a[17], x.invT, g);
+    b.Gp[k] = ck_exp2(g, tab);
+    b.Gm[k] = ck_exp2(-g, tab);
     b.cpR[k] = fma(a[4], x.T4, fma(a[3], x.T3, fma(a[2], x.T2, fma(a[1], x.T, a[0]))));
     b.hRT[k] = fma(a[10], x.invT, fma(a[9], x.T4, fma(a[8], x.T3, fma(a[7], x.T2, fma(a[6], x.T, a[5])))));
-    if (want_dcp) b.dcpR[k] = fma(4.0 * a[4], x.T3, fma(3.0 * a[3], x.T2, fma(2.0 * a[2], x.T, a[1])));
+    if (want_dcp)
+      dcpm = fma(y[1 + k] * m.invW[k], fma(4.0 * a[4], x.T3, fma(3.0 * a[3], x.T2, fma(2.0 * a[2], x.T, a[1]))), dcpm);
     b.wd[k] = 0.0;
     b.aT[k] = 0.0;
     b.E[k] = 0.0;
     b.u[k] = 0.0;
   }
+  x.dcpm = dcpm;
   x.Ctot = team_sum(c, b.red);
 }
 
@@ -96,7 +102,6 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
                                               bool want_jac) {
   // i: index of the reaction inside the current chunk
   const double* X = b.X;
-  const double* g2 = b.g2;
   const double l2kf = fma(-r.EoR2, x.invT, fma(r.beta, x.log2T, r.lA2));
   const double kf = ck_exp2(l2kf, tab);
   double fwd = X[r.sp[0]];
@@ -116,14 +121,14 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
       dlnkc = dlnkf - fma(ra[2] * LN2, x.invT, ra[1]) * x.invT;
     }
   } else if (r.rev) {
-    double l2kc = r.dnu_d * (LOG2_P0_OVER_R - x.log2T);
-    l2kc += g2[r.sp[3]];
-    if (r.nprod > 1) l2kc += g2[r.sp[4]];
-    if (r.nprod > 2) l2kc += g2[r.sp[5]];
-    l2kc -= g2[r.sp[0]];
-    if (r.nreac > 1) l2kc -= g2[r.sp[1]];
-    if (r.nreac > 2) l2kc -= g2[r.sp[2]];
-    kr = ck_exp2(l2kf - l2kc, tab);
+    // 1/K_c = (R T/p0)^dnu prod_reactants Gp prod_products Gm (Eq. kc)
+    double kci = rt_over_p0_pow(r.dnu, x.T, x.invT) * b.Gp[r.sp[0]];
+    kci *= b.Gm[r.sp[3]];
+    if (r.nreac > 1) kci *= b.Gp[r.sp[1]];
+    if (r.nprod > 1) kci *= b.Gm[r.sp[4]];
+    if (r.nreac > 2) kci *= b.Gp[r.sp[2]];
+    if (r.nprod > 2) kci *= b.Gm[r.sp[5]];
+    kr = kf * kci;
     rv = X[r.sp[3]];
     if (r.nprod > 1) rv *= X[r.sp[4]];
     if (r.nprod > 2) rv *= X[r.sp[5]];
@@ -212,7 +217,7 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
 static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab, double p,
                                              const double* y, double* f, TeamBufs b) {
   Mix x;
-  team_species(m, p, y, b, x, false);
+  team_species(m, p, y, b, x, false, tab);
   team_sync();
   const int NC = m.n_chunks, CH = m.chunk;
   for (int c = 0; c < NC; ++c) {
@@ -263,7 +268,7 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
 static __device__ void team_jacobian(const DevMech& m, const double* tab, double p, const double* y,
                               double* f, double* J, TeamBufs& b, Mix& x) {
   const int S = m.S, n = m.n;
-  team_species(m, p, y, b, x, true);
+  team_species(m, p, y, b, x, true, tab);
   // species block A starts at zero; chunk by chunk, every entry touched by
   // the chunk adds its fixed-order sum of contributions (one thread per
   // entry, no conflicts), and every species adds its terms of wdot,
@@ -309,12 +314,11 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   // W_k/W_j, so J holds A'_kj = W_k A_kj / W_j here.
   const double invrho = 1.0 / x.rho;
   const double cvf = m.cv ? 1.0 : 0.0, cpf = 1.0 - cvf;
-  double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = 0.0, cw = 0.0, ha = 0.0, eu = 0.0;
+  double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = x.dcpm, cw = 0.0, ha = 0.0, eu = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const double yk = y[1 + k] * m.invW[k];
     const double e = b.hRT[k] - cvf, c = b.cpR[k] - cvf;
     cpm = fma(yk, c, cpm);
-    dcpm = fma(yk, b.dcpR[k], dcpm);
     hw = fma(e, b.wd[k], hw);
     he = fma(b.hRT[k], b.E[k], he);
     cw = fma(c, b.wd[k], cw);

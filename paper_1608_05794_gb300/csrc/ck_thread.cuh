@@ -23,11 +23,12 @@ struct MechView {
 };
 
 // f = (dT/dt, dY_k/dt) at state y (Eqs. ydot, tdot, wdot, kfor, krev, kc,
-// tfits).  y and f are strided (element k at y[k*ys]); X, g2, wd are per-lane
-// scratch of S doubles.
+// tfits).  y and f are strided (element k at y[k*ys]); X and wd are per-lane
+// scratch of S doubles, G of 2S (the species factors 2^(g_k), 2^(-g_k)).
 //   rho = p Wbar / (R T), [X_k] = rho Y_k / W_k,
 //   k_f = 2^(log2 A + beta log2 T - Ea/(R T ln 2)),
-//   log2 K_c = sum_j nu_j g_j / ln 2 + dnu log2(p0/(R T)), k_r = 2^(log2 k_f - log2 K_c),
+//   1/K_c = (R T/p0)^dnu prod_reactants 2^(g_j) prod_products 2^(-g_j), g_j = (S/R - H/RT)_j / ln 2,
+//   k_r = k_f / K_c,
 //   c = 1, [M], or P_r/(1+P_r) with P_r = 2^(log2 k0 - log2 k_inf) [M],
 //   q = c (k_f prod [X]^nu' - k_r prod [X]^nu''),  wdot_k = sum (nu'' - nu') q,
 //   dY_k/dt = wdot_k W_k / rho, dT/dt = -T sum_k (H_k/RT) wdot_k / (rho sum_k Y_k (cp_k/R)/W_k).
@@ -35,7 +36,7 @@ struct MechView {
 // Constant volume (Sec. 3): rho = p (the parameter is the density) and
 // H/RT -> U/RT = H/RT - 1, cp/R -> cv/R = cp/R - 1 in dT/dt.
 __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const double* y, int ys,
-                                           double* f, int fs, double* X, double* g2, double* wd) {
+                                           double* f, int fs, double* X, double* G, double* wd) {
   const int S = m.S;
   const double T = y[0];
   const double invT = 1.0 / T;
@@ -56,10 +57,12 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
     g = fma(a[14], T2, g);
     g = fma(a[15], T3, g);
     g = fma(a[16], T4, g);
-    g2[k] = fma(a[17], invT, g);
+    g = fma(a[17], invT, g);
+    G[k] = ck_exp2(g, m.tab);
+    G[S + k] = ck_exp2(-g, m.tab);
     wd[k] = 0.0;
   }
-  const double lp2 = LOG2_P0_OVER_R - log2T;  // log2(p0 / (R T))
+  const double* Gm = G + S;
   for (int i = 0; i < m.R; ++i) {
     const RxnRec& r = m.rx[i];
     const double l2kf = fma(-r.EoR2, invT, fma(r.beta, log2T, r.lA2));
@@ -76,14 +79,13 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
       if (r.nprod > 2) rv *= X[r.sp[5]];
       net = fma(-kr, rv, net);
     } else if (r.rev) {
-      double l2kc = r.dnu_d * lp2;
-      l2kc += g2[r.sp[3]];
-      if (r.nprod > 1) l2kc += g2[r.sp[4]];
-      if (r.nprod > 2) l2kc += g2[r.sp[5]];
-      l2kc -= g2[r.sp[0]];
-      if (r.nreac > 1) l2kc -= g2[r.sp[1]];
-      if (r.nreac > 2) l2kc -= g2[r.sp[2]];
-      const double kr = ck_exp2(l2kf - l2kc, m.tab);
+      double kci = rt_over_p0_pow(r.dnu, T, invT) * G[r.sp[0]];
+      kci *= Gm[r.sp[3]];
+      if (r.nreac > 1) kci *= G[r.sp[1]];
+      if (r.nprod > 1) kci *= Gm[r.sp[4]];
+      if (r.nreac > 2) kci *= G[r.sp[2]];
+      if (r.nprod > 2) kci *= Gm[r.sp[5]];
+      const double kr = kf * kci;
       double rv = X[r.sp[3]];
       if (r.nprod > 1) rv *= X[r.sp[4]];
       if (r.nprod > 2) rv *= X[r.sp[5]];
