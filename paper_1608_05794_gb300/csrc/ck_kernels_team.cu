@@ -222,7 +222,7 @@ __device__ void refined_solve(const double* M64, const float* M32, int n, const 
   const int tid = threadIdx.x, P = blockDim.x;
   for (int i = tid; i < n; i += P) xf[i] = (float)u[i];
   __syncthreads();
-  if (tid < 32) warp_lu_solve(M32, n, piv, invd32, xf);
+  if (tid < 32) warp_lu_solve<true>(M32, n, piv, invd32, xf);
   __syncthreads();
   for (int i = tid; i < n; i += P) x[i] = (double)xf[i];
   __syncthreads();
@@ -241,7 +241,7 @@ __device__ void refined_solve(const double* M64, const float* M32, int n, const 
       xf[i] = (float)((s0 + s1) + (s2 + s3));
     }
     __syncthreads();
-    if (tid < 32) warp_lu_solve(M32, n, piv, invd32, xf);
+    if (tid < 32) warp_lu_solve<true>(M32, n, piv, invd32, xf);
     __syncthreads();
     for (int i = tid; i < n; i += P) x[i] += (double)xf[i];
     __syncthreads();
@@ -319,11 +319,11 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
         team_sync();
         int info;
         if (PREC == 0) {
-          info = lu_reg<G, T>(M, n, piv, invd, lb, ub, b.red);
+          info = lu_reg<G, T, true>(M, n, piv, invd, lb, ub, b.red);
         } else {
           for (int e = tid; e < n * n; e += P) M32[e] = (float)M[e];
           __syncthreads();
-          info = lu_reg<G, T>(M32, n, piv, reinterpret_cast<float*>(invd), reinterpret_cast<float*>(lb),
+          info = lu_reg<G, T, true>(M32, n, piv, reinterpret_cast<float*>(invd), reinterpret_cast<float*>(lb),
                               reinterpret_cast<float*>(ub), b.red);
         }
         if (info) {
@@ -339,7 +339,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
         for (int i = tid; i < n; i += P) u1[i] = F0[i];
         team_sync();
         if (PREC == 0) {
-          if (tid < 32) warp_lu_solve(M, n, piv, invd, u1);
+          if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u1);
           __syncthreads();
         } else {
           refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u1, reinterpret_cast<float*>(u4), Yt, PREC);
@@ -351,7 +351,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
         for (int i = tid; i < n; i += P) u2[i] = fma(ROS_C21 * ih, u1[i], F[i]);
         team_sync();
         if (PREC == 0) {
-          if (tid < 32) warp_lu_solve(M, n, piv, invd, u2);
+          if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u2);
           __syncthreads();
         } else {
           refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u2, reinterpret_cast<float*>(u4), Yt, PREC);
@@ -364,7 +364,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
           u3[i] = fma(ROS_C32 * ih, u2[i], fma(ROS_C31 * ih, u1[i], F[i]));
         team_sync();
         if (PREC == 0) {
-          if (tid < 32) warp_lu_solve(M, n, piv, invd, u3);
+          if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u3);
           __syncthreads();
         } else {
           refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u3, reinterpret_cast<float*>(u4), Yt, PREC);
@@ -374,7 +374,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
           u4[i] = fma(ROS_C43 * ih, u3[i], fma(ROS_C42 * ih, u2[i], fma(ROS_C41 * ih, u1[i], F[i])));
         team_sync();
         if (PREC == 0) {
-          if (tid < 32) warp_lu_solve(M, n, piv, invd, u4);
+          if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u4);
           __syncthreads();
         } else {
           refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u4, reinterpret_cast<float*>(F), Yt, PREC);

@@ -57,15 +57,37 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
                                              TeamBufs& b, Mix& x, bool want_dcp, const double* tab) {
   const int S = m.S;
   x.T = y[0];
-  x.invT = 1.0 / x.T;
-  x.lnT = log(x.T);
-  x.log2T = x.lnT * INV_LN2;
-  x.T2 = x.T * x.T;
-  x.T3 = x.T2 * x.T;
-  x.T4 = x.T3 * x.T;
+  // the temperature functions are formed by the first warp alone (an FP64
+  // instruction costs every warp that issues it a full slot) and handed to
+  // the others through red[40..45] across the barriers of the sum below
+  double* tf = b.red + 40;
+  if (threadIdx.x < 32) {
+    x.invT = 1.0 / x.T;
+    x.lnT = log(x.T);
+    x.log2T = x.lnT * INV_LN2;
+    x.T2 = x.T * x.T;
+    x.T3 = x.T2 * x.T;
+    x.T4 = x.T3 * x.T;
+    if (threadIdx.x == 0) {
+      tf[0] = x.invT;
+      tf[1] = x.lnT;
+      tf[2] = x.log2T;
+      tf[3] = x.T2;
+      tf[4] = x.T3;
+      tf[5] = x.T4;
+    }
+  }
   double s = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) s = fma(y[1 + k], m.invW[k], s);
   const double sumYW = team_sum(s, b.red);
+  if (threadIdx.x >= 32) {
+    x.invT = tf[0];
+    x.lnT = tf[1];
+    x.log2T = tf[2];
+    x.T2 = tf[3];
+    x.T3 = tf[4];
+    x.T4 = tf[5];
+  }
   x.Wbar = 1.0 / sumYW;
   x.rho = m.cv ? p : p / (R_GAS * x.T * sumYW);  // constant volume: p is the density
   double c = 0.0, dcpm = 0.0;
@@ -394,10 +416,17 @@ __device__ __forceinline__ unsigned long long abs_key(float v) {
 __device__ __forceinline__ unsigned long long inf_key(double) { return 0x7ff0000000000000ULL; }
 __device__ __forceinline__ unsigned long long inf_key(float) { return 0x7f800000ULL; }
 
-template <int G, int T, class F>
+// PRE = false: piv[k] receives the row swapped with row k (LAPACK order) and
+// A the factors.  PRE = true (the form the stage solves of ROS4 take): piv
+// receives the composite row permutation (row i of PA is row piv[i] of A),
+// and the strict upper triangle of U is stored pre-divided by its diagonal,
+// so that a solve gathers b once and needs no division in back substitution.
+template <int G, int T, bool PRE = false, class F>
 __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red) {
   const int tid = threadIdx.x, tr = tid / G, tc = tid - tr * G;
   const unsigned long long INFB = inf_key(F(0));
+  if (PRE)
+    for (int i = tid; i < n; i += blockDim.x) piv[i] = i;
   F a[T][T];
 #pragma unroll
   for (int r = 0; r < T; ++r)
@@ -481,7 +510,13 @@ __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red)
     }
     // 3. unscaled column k below the diagonal, the pivot row, the reciprocal
     if (tid == 0) {
-      piv[k] = p;
+      if (PRE) {
+        const int t = piv[k];
+        piv[k] = piv[p];
+        piv[p] = t;
+      } else {
+        piv[k] = p;
+      }
       invd[k] = F(1) / pv;
     }
     if (tc == kt) {
@@ -531,12 +566,15 @@ __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red)
   }
   __syncthreads();
 #pragma unroll
-  for (int r = 0; r < T; ++r)
+  for (int r = 0; r < T; ++r) {
+    const int i = tr + G * r;
+    const F di = (PRE && i < n) ? invd[i] : F(1);
 #pragma unroll
     for (int c = 0; c < T; ++c) {
-      const int i = tr + G * r, j = tc + G * c;
-      if (i < n && j < n) A[i * n + j] = a[r][c];
+      const int j = tc + G * c;
+      if (i < n && j < n) A[i * n + j] = (PRE && j > i) ? a[r][c] * di : a[r][c];
     }
+  }
   __syncthreads();
   return info;
 }
@@ -547,10 +585,26 @@ __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red)
 // earlier blocks is a matrix-vector product (one row per lane, four partial
 // sums in a fixed order), the diagonal block a substitution whose solved
 // value is broadcast by a shuffle.
-template <class F>
+// PRE: the factors and permutation come from lu_reg<G, T, true> (gather by
+// the composite permutation, U pre-divided by its diagonal).
+template <bool PRE = false, class F>
 __device__ __forceinline__ void warp_lu_solve(const F* A, int n, const int* piv, const F* invd, F* b) {
   const int lane = threadIdx.x & 31;
-  if (lane == 0) {
+  if (PRE) {
+    constexpr int MAXR = 5;  // n <= 160 (the team kernels take n <= 144)
+    F g[MAXR];
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int i = lane + 32 * q;
+      g[q] = i < n ? b[piv[i]] : F(0);
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < MAXR; ++q) {
+      const int i = lane + 32 * q;
+      if (i < n) b[i] = g[q];
+    }
+  } else if (lane == 0) {
     for (int k = 0; k < n; ++k) {
       const int p = piv[k];
       if (p != k) {
@@ -591,7 +645,7 @@ __device__ __forceinline__ void warp_lu_solve(const F* A, int n, const int* piv,
     const int i = B1 + lane;
     const bool act = i < n;
     const int m = min(32, n - B1);
-    F s0 = act ? b[i] : F(0), s1 = F(0), s2 = F(0), s3 = F(0);
+    F s0 = act ? (PRE ? b[i] * invd[i] : b[i]) : F(0), s1 = F(0), s2 = F(0), s3 = F(0);
     if (act) {
       const F* Ui = A + (size_t)i * n;
       int j = B1 + 32;
@@ -605,7 +659,7 @@ __device__ __forceinline__ void warp_lu_solve(const F* A, int n, const int* piv,
     }
     F s = (s0 + s1) + (s2 + s3);
     for (int jj = m - 1; jj >= 0; --jj) {
-      if (lane == jj) s *= invd[i];
+      if (!PRE && lane == jj) s *= invd[i];
       const F xj = __shfl_sync(0xffffffffu, s, jj);
       if (act && lane < jj) s = fma(-A[(size_t)i * n + B1 + jj], xj, s);
     }
