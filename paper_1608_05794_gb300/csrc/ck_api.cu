@@ -766,10 +766,13 @@ int ck_integrate_ros4_noalloc(const ck_mech* m, int64_t n, const double* p, doub
   if (!(o.rtol > 0.0) || !(o.atol > 0.0) || o.max_steps < 1 || !(o.h0 >= 0.0) || !(o.fixed_h >= 0.0))
     return fail(CK_EINVAL, "opts: need rtol > 0, atol > 0, max_steps >= 1, h0 >= 0, fixed_h >= 0");
   if (o.precision != 0) return fail(CK_EINVAL, "opts.precision: only 0 (FP64) is available");
+  if (o.jac < 0 || o.jac > 1) return fail(CK_EINVAL, "opts.jac must be 0 or 1");
+  if (!(o.team == 0 || o.team == 8 || o.team == 16)) return fail(CK_EINVAL, "opts.team must be 0, 8 or 16");
   if (int rc = check_device(m)) return rc;
   ck::SolverParams sp{o.rtol, o.atol, o.h0, o.fixed_h, o.max_steps, o.jac};
   ck::LaunchCfg cfg;
   if (o.variant > 0) cfg.ctas_per_sm = o.variant;
+  cfg.grid_side = o.team;
   cudaError_t e = ck::launch_ros4_noalloc(m->hm, n, p, y, dt, h_inout, sp, steps, status,
                                          static_cast<cudaStream_t>(stream), cfg);
   return e == cudaSuccess ? CK_OK : cuda_fail(e, "ck_integrate_ros4_noalloc");

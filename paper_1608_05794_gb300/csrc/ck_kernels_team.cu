@@ -213,7 +213,8 @@ __device__ double team_h0(const DevMech& d, const double* tab, double p, const d
 
 // Stage solve of the precision form: the iteration matrix is factored in
 // FP32 (M32, piv, invd32) and each solve is refined against the FP64 matrix
-// M64: x = LU32^-1 b, then REFINE times r = b - M64 x (FP64), x += LU32^-1 r.
+// M64 (the CTA's copy in global memory, L2-resident): x = LU32^-1 b, then
+// REFINE times r = b - M64 x (FP64), x += LU32^-1 r.
 // b (in u) is overwritten with x; xf (n floats) and x (n doubles) are scratch
 // that must not hold anything the caller still needs (stage 4 reuses the
 // third stage's f, so the first three solves take u4's buffer as xf).
@@ -252,12 +253,16 @@ __device__ void refined_solve(const double* M64, const float* M32, int n, const 
 
 // PREC 0: FP64 LU and solves.  PREC 1 / 2: FP32 LU and solves with one /
 // two steps of FP64 iterative refinement (the rates, K_c, the temperature
-// equation, the error norm and the step control stay FP64).
+// equation, the error norm and the step control stay FP64).  The precision
+// form keeps its FP64 iteration matrix, which the refinement needs, in
+// m64g[blockIdx.x][n][n] (global memory; 21 MB for 912 CTAs at n = 54, so it
+// stays in L2) and its FP32 factors in the first half of the shared FP64
+// matrix, so both forms need the same shared memory and residency.
 template <int G, int T, int PREC>
-__global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
+__global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
                                                  double* __restrict__ y, const double* __restrict__ dt,
                                                  double* h_io, SolverParams sp, int32_t* steps,
-                                                 int32_t* status, int32_t* queue) {
+                                                 int32_t* status, int32_t* queue, double* __restrict__ m64g) {
   extern __shared__ __align__(16) double sm[];
   __shared__ int slot;
   const int n = d.n;
@@ -276,7 +281,8 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
   double* lb = F;   // LU broadcast buffers: F and Yt are free while factoring
   double* ub = Yt;
   TeamBufs b = carve_bufs(invd + n + (n + 1) / 2, d.S, d.chunk);
-  float* M32 = reinterpret_cast<float*>(b.red + 48);  // PREC >= 1 only: n x n floats
+  float* M32 = reinterpret_cast<float*>(M);  // PREC >= 1: FP32 factors over the FP64 matrix
+  double* Mg = PREC ? m64g + (size_t)blockIdx.x * n * n : nullptr;
   Mix x;
   const bool fixed = sp.fixed_h > 0.0;
   const int tid = threadIdx.x, P = blockDim.x;
@@ -321,7 +327,9 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
         if (PREC == 0) {
           info = lu_reg<G, T, true>(M, n, piv, invd, lb, ub, b.red);
         } else {
-          for (int e = tid; e < n * n; e += P) M32[e] = (float)M[e];
+          for (int e = tid; e < n * n; e += P) Mg[e] = M[e];
+          __syncthreads();
+          for (int e = tid; e < n * n; e += P) M32[e] = (float)Mg[e];
           __syncthreads();
           info = lu_reg<G, T, true>(M32, n, piv, reinterpret_cast<float*>(invd), reinterpret_cast<float*>(lb),
                               reinterpret_cast<float*>(ub), b.red);
@@ -342,7 +350,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u1);
           __syncthreads();
         } else {
-          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u1, reinterpret_cast<float*>(u4), Yt, PREC);
+          refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u1, reinterpret_cast<float*>(u4), Yt, PREC);
         }
         // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
         for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A21, u1[i], yv[i]);
@@ -354,7 +362,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u2);
           __syncthreads();
         } else {
-          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u2, reinterpret_cast<float*>(u4), Yt, PREC);
+          refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u2, reinterpret_cast<float*>(u4), Yt, PREC);
         }
         // stage 3: M u3 = f(y + a31 u1 + a32 u2) + (c31 u1 + c32 u2)/h
         for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A32, u2[i], fma(ROS_A31, u1[i], yv[i]));
@@ -367,7 +375,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u3);
           __syncthreads();
         } else {
-          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u3, reinterpret_cast<float*>(u4), Yt, PREC);
+          refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u3, reinterpret_cast<float*>(u4), Yt, PREC);
         }
         // stage 4: same argument as stage 3 (a4j = a3j, a43 = 0), so f is reused
         for (int i = tid; i < n; i += P)
@@ -377,7 +385,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? (PREC ? 4 : 6) : 1) k_ros4(con
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u4);
           __syncthreads();
         } else {
-          refined_solve(M, M32, n, piv, reinterpret_cast<const float*>(invd), u4, reinterpret_cast<float*>(F), Yt, PREC);
+          refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u4, reinterpret_cast<float*>(F), Yt, PREC);
         }
         // y* = y + sum m_i u_i (into Yt), e = sum E_i u_i (into F)
         int nf = 0;
@@ -598,9 +606,8 @@ static int team_grid(K kernel, int threads, size_t smem, int64_t work, const Lau
   return (int)(g < 1 ? 1 : g);
 }
 
-size_t ros4_smem_bytes(int n, int S, int chunk, int prec) {
-  return sizeof(double) * ((size_t)n * n + 9 * (size_t)n + (n + 1) / 2 + team_bufs_doubles(S, chunk)) +
-         (prec ? sizeof(float) * (size_t)n * n : 0);
+size_t ros4_smem_bytes(int n, int S, int chunk) {
+  return sizeof(double) * ((size_t)n * n + 9 * (size_t)n + (n + 1) / 2 + team_bufs_doubles(S, chunk));
 }
 
 // Thread grid of the register-tiled LU for dimension n: G x G threads with
@@ -666,15 +673,27 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
                         int32_t* queue, cudaStream_t st, const LaunchCfg& cfg) {
   if (n <= 0) return cudaSuccess;
   const int nn = hm.d.n;
-  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.d.chunk, cfg.precision);
+  const size_t smem = ros4_smem_bytes(nn, hm.S, hm.d.chunk);
   cudaError_t e = cudaMemsetAsync(queue, 0, sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   return with_grid(nn, [&](auto Gc, auto Tc) {
     constexpr int G = decltype(Gc)::value, T = decltype(Tc)::value;
     auto kern = cfg.precision == 2 ? k_ros4<G, T, 2> : (cfg.precision == 1 ? k_ros4<G, T, 1> : k_ros4<G, T, 0>);
     const int grid = team_grid(kern, G * G, smem, n, cfg);
-    kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue);
-    return cudaGetLastError();
+    double* m64g = nullptr;
+    if (cfg.precision) {
+      // the precision form's per-CTA FP64 matrices, stream-ordered
+      cudaError_t a = cudaMallocAsync(reinterpret_cast<void**>(&m64g),
+                                      sizeof(double) * (size_t)grid * nn * nn, st);
+      if (a != cudaSuccess) return a;
+    }
+    kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue, m64g);
+    cudaError_t k = cudaGetLastError();
+    if (m64g) {
+      cudaError_t f = cudaFreeAsync(m64g, st);
+      if (k == cudaSuccess) k = f;
+    }
+    return k;
   }, cfg.grid_side);
 }
 
@@ -726,6 +745,7 @@ cudaError_t launch_ros4_noalloc(const HostMech& hm, int64_t n, const double* p, 
                                 const double* dt, double* h_io, const SolverParams& sp,
                                 int32_t* steps, int32_t* status, cudaStream_t st,
                                 const LaunchCfg& cfg) {
+  if (cfg.precision) return cudaErrorNotSupported;  // its FP64 matrices need an allocation
   int32_t* queue = nullptr;
   cudaError_t e = noalloc_scratch(&queue);
   if (e != cudaSuccess) return e;
