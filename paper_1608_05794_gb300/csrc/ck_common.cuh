@@ -17,7 +17,6 @@ constexpr double R_GAS = 8.314462618;       // J/(mol K)
 constexpr double P_STD = 101325.0;          // p0 of Eq. kc, Pa
 constexpr double LN2 = 0.6931471805599453094;
 constexpr double INV_LN2 = 1.4426950408889634074;
-constexpr double LOG2_P0_OVER_R = 13.573007627848395117;  // log2(101325 / 8.314462618)
 constexpr double R_OVER_P0 = R_GAS / P_STD;               // R T / p0 is the molar volume at p0, m^3/mol
 constexpr double P0_OVER_R = P_STD / R_GAS;
 
@@ -101,10 +100,6 @@ struct DevMech {
 // polynomial in r ln 2 (truncation < 4e-17 relative).  The reduction is
 // exact (x - round_{1/256}(x) is representable), so the result is within
 // about one ulp.  |x| > 1000 falls back to the library exp2.
-struct Exp2Table {
-  double t[256];
-};
-
 __device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ tab) {
   if (!(fabs(x) <= 1000.0)) return exp2(x);
   const double SHIFT = 26388279066624.0;  // 1.5 * 2^44: ulp 2^-8

@@ -98,11 +98,11 @@ __global__ void __launch_bounds__(128) k_rhs(DevMech d, StageLayout L, int stage
     base = smem + STAGE_HDR;
   }
   const MechView m = view_of(d, L, base);
-  double X[MAXS], g2[2 * MAXS], wd[MAXS];
+  double X[MAXS], G[2 * MAXS], wd[MAXS];
   const int n = d.n;
   for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
        r += (int64_t)gridDim.x * blockDim.x) {
-    rhs_thread(m, p[r], y + r * n, 1, f + r * n, 1, X, g2, wd);
+    rhs_thread(m, p[r], y + r * n, 1, f + r * n, 1, X, G, wd);
   }
 }
 
@@ -122,8 +122,8 @@ __device__ __forceinline__ double wrms_thread(int n, const double* e, const doub
 // order 4, weights atol + rtol |y0|).  f0, y1, f1 are scratch vectors.
 __device__ double h0_thread(const MechView& m, int n, double p, const double* y0, double tspan,
                             double rtol, double atol, double* f0, double* y1, double* f1, double* X,
-                            double* g2, double* wd) {
-  rhs_thread(m, p, y0, 1, f0, 1, X, g2, wd);
+                            double* G, double* wd) {
+  rhs_thread(m, p, y0, 1, f0, 1, X, G, wd);
   double d0 = 0.0, d1 = 0.0;
   for (int i = 0; i < n; ++i) {
     const double sc = atol + rtol * fabs(y0[i]);
@@ -134,7 +134,7 @@ __device__ double h0_thread(const MechView& m, int n, double p, const double* y0
   d1 = sqrt(d1 / n);
   const double ha = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 : 0.01 * d0 / d1;
   for (int i = 0; i < n; ++i) y1[i] = fma(ha, f0[i], y0[i]);
-  rhs_thread(m, p, y1, 1, f1, 1, X, g2, wd);
+  rhs_thread(m, p, y1, 1, f1, 1, X, G, wd);
   double d2 = 0.0;
   for (int i = 0; i < n; ++i) {
     const double sc = atol + rtol * fabs(y0[i]);
@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(128) k_rkf45(DevMech d, StageLayout L, int sta
   }
   const MechView m = view_of(d, L, base);
   constexpr int MAXN = MAXS + 1;
-  double X[MAXS], g2[2 * MAXS], wd[MAXS];
+  double X[MAXS], G[2 * MAXS], wd[MAXS];
   double yv[MAXN], yt[MAXN], k[6][MAXN];
   const int n = d.n;
   const bool fixed = sp.fixed_h > 0.0;
@@ -199,7 +199,7 @@ __global__ void __launch_bounds__(128) k_rkf45(DevMech d, StageLayout L, int sta
       } else if (sp.h0 > 0.0) {
         h = sp.h0;
       } else {
-        h = h0_thread(m, n, pr, yv, tf, sp.rtol, sp.atol, k[0], yt, k[1], X, g2, wd);
+        h = h0_thread(m, n, pr, yv, tf, sp.rtol, sp.atol, k[0], yt, k[1], X, G, wd);
       }
     }
     if (!finish) {
@@ -213,28 +213,28 @@ __global__ void __launch_bounds__(128) k_rkf45(DevMech d, StageLayout L, int sta
         finish = true;
       } else {
         // stages k_s = hh f(y + sum_j a_sj k_j)
-        rhs_thread(m, pr, yv, 1, k[0], 1, X, g2, wd);
+        rhs_thread(m, pr, yv, 1, k[0], 1, X, G, wd);
         for (int i = 0; i < n; ++i) k[0][i] *= hh;
         for (int i = 0; i < n; ++i) yt[i] = fma(RK_A21, k[0][i], yv[i]);
-        rhs_thread(m, pr, yt, 1, k[1], 1, X, g2, wd);
+        rhs_thread(m, pr, yt, 1, k[1], 1, X, G, wd);
         for (int i = 0; i < n; ++i) k[1][i] *= hh;
         for (int i = 0; i < n; ++i) yt[i] = fma(RK_A32, k[1][i], fma(RK_A31, k[0][i], yv[i]));
-        rhs_thread(m, pr, yt, 1, k[2], 1, X, g2, wd);
+        rhs_thread(m, pr, yt, 1, k[2], 1, X, G, wd);
         for (int i = 0; i < n; ++i) k[2][i] *= hh;
         for (int i = 0; i < n; ++i)
           yt[i] = fma(RK_A43, k[2][i], fma(RK_A42, k[1][i], fma(RK_A41, k[0][i], yv[i])));
-        rhs_thread(m, pr, yt, 1, k[3], 1, X, g2, wd);
+        rhs_thread(m, pr, yt, 1, k[3], 1, X, G, wd);
         for (int i = 0; i < n; ++i) k[3][i] *= hh;
         for (int i = 0; i < n; ++i)
           yt[i] = fma(RK_A54, k[3][i],
                       fma(RK_A53, k[2][i], fma(RK_A52, k[1][i], fma(RK_A51, k[0][i], yv[i]))));
-        rhs_thread(m, pr, yt, 1, k[4], 1, X, g2, wd);
+        rhs_thread(m, pr, yt, 1, k[4], 1, X, G, wd);
         for (int i = 0; i < n; ++i) k[4][i] *= hh;
         for (int i = 0; i < n; ++i)
           yt[i] = fma(RK_A65, k[4][i],
                       fma(RK_A64, k[3][i],
                           fma(RK_A63, k[2][i], fma(RK_A62, k[1][i], fma(RK_A61, k[0][i], yv[i])))));
-        rhs_thread(m, pr, yt, 1, k[5], 1, X, g2, wd);
+        rhs_thread(m, pr, yt, 1, k[5], 1, X, G, wd);
         for (int i = 0; i < n; ++i) k[5][i] *= hh;
         // y* = y + sum b k (into yt), e = sum (bh - b) k (into k[1], whose b is 0)
         bool nf = false;
