@@ -659,6 +659,49 @@ def run_variants(args):
     print(json.dumps(line), flush=True)
 
 
+def run_precision(args):
+    """ROS4 in the FP64 form and the precision forms (FP32 LU and solves with
+    one or two FP64 refinement steps) on the medium and large workloads;
+    reports integrations/s and the largest final-state difference from the
+    FP64 form (the parity tests compare every form with the oracle)."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from synth.configs import CONFIGS, load_mechanism, reactor_states
+    res = {}
+    for name, N in (("medium", args.precision_reactors), ("large", args.precision_reactors // 2)):
+        cfg = CONFIGS[name]
+        gm = ck.load_mechanism(load_mechanism(cfg["mech"]))
+        y_np, p_np = reactor_states(name, n=N)
+        y0 = torch.as_tensor(y_np, device="cuda")
+        p = torch.as_tensor(p_np, device="cuda")
+        dt = torch.full((N,), cfg["dt"], dtype=torch.float64, device="cuda")
+        st = torch.empty(N, dtype=torch.int32, device="cuda")
+        out, finals = {}, {}
+        for prec in (0, 1, 2):
+            y = torch.empty_like(y0)
+            ts = []
+            for i in range(args.warmup + args.steps):
+                y.copy_(y0)
+                a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record()
+                ck.integrate_ros4(gm, p, y, dt, st, opts=ck.SolverOpts.make(precision=prec))
+                b.record()
+                torch.cuda.synchronize()
+                if i >= args.warmup:
+                    ts.append(a.elapsed_time(b) / 1e3)
+            finals[prec] = y.cpu().numpy()
+            out[f"precision_{prec}"] = {"integrations_per_s": N / float(np.mean(ts)),
+                                        "all_ok": bool((st == 0).all().item())}
+        for prec in (1, 2):
+            d = finals[prec] - finals[0]
+            out[f"precision_{prec}"]["max_rel_dT_vs_fp64"] = float(np.max(np.abs(d[:, 0]) / finals[0][:, 0]))
+            out[f"precision_{prec}"]["max_abs_dY_vs_fp64"] = float(np.max(np.abs(d[:, 1:])))
+        res[f"{name} ({N} reactors)"] = out
+    print(json.dumps({"mode": "precision", "metric": "ROS4 reactor integrations/s, FP64 vs FP32 LU + FP64 refinement",
+                      "dt": "each workload's", "results": res}), flush=True)
+
+
 def run_profile_case(args):
     """A small case of one kernel for ncu (warm-up launches, then 3 launches)."""
     import torch
@@ -700,7 +743,8 @@ def main():
                     help="profiling only: launch one kernel a few times on a small batch, print no bench line")
     ap.add_argument("--reactors", type=int, default=2048, help="batch size of --profile-case")
     ap.add_argument("--dt", type=float, default=None, help="dt of --profile-case (default: the workload's)")
-    ap.add_argument("--mode", choices=["bench", "serve", "batch", "fdjac", "variants"], default="bench")
+    ap.add_argument("--mode", choices=["bench", "serve", "batch", "fdjac", "variants", "precision"], default="bench")
+    ap.add_argument("--precision-reactors", type=int, default=32768, help="precision: medium reactors (large: half)")
     ap.add_argument("--variant-reactors", type=int, default=32768, help="variants: medium-workload reactors")
     ap.add_argument("--rhs-repeats-variant", type=int, default=20, help="variants: RHS passes per timing")
     ap.add_argument("--fd-reactors", type=int, default=8192, help="fdjac: medium-workload reactors")
@@ -718,6 +762,8 @@ def main():
         run_fdjac(args)
     elif args.mode == "variants":
         run_variants(args)
+    elif args.mode == "precision":
+        run_precision(args)
     elif args.mode == "batch":
         run_batch(args)
     elif args.profile_case:
