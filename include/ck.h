@@ -241,9 +241,12 @@ int ck_graph_cache_clear(void);
  * A request is admitted, in arrival order, once its device footprint
  * (n * ((S+1)*8 + 28) bytes: state, p, dt, status, step counts) fits the
  * HBM budget; admitted requests are split into chunks of chunk_reactors
- * reactors that a dispatcher thread launches round-robin on `streams` CUDA
- * streams, so work that arrives while other requests run starts at once and
- * overlaps them on the device.  A request's arrays are all host memory
+ * reactors that a dispatcher thread launches on `streams` CUDA streams, each
+ * free stream taking the next chunk of the request with the least estimated
+ * remaining work (reactors left x the FP64 cost of one step of its method;
+ * a request admitted more than 30 s earlier goes first).  Work that arrives
+ * while other requests run therefore starts at once, overlaps them on the
+ * device, and short requests are not held behind long ones.  A request's arrays are all host memory
  * (staged by the server; pin them for asynchronous copies) or all device
  * memory (used in place), and must stay valid until the request is done.
  * Each reactor is integrated independently, so results do not depend on the

@@ -3,7 +3,11 @@
 // Requests (a batch of reactors on one mechanism, ROS4 or RKF45) are admitted
 // in arrival order while their device footprint fits the HBM budget; an
 // admitted request is split into chunks of reactors, and a dispatcher thread
-// launches chunks of all admitted requests round-robin on a pool of streams.
+// launches chunks on a pool of streams, each free stream taking the next
+// chunk of the admitted request with the least estimated remaining work
+// (reactors left x FP64 cost of one step of its method, from ck_count_work):
+// short requests overtake long ones, which cuts the median latency; a request
+// admitted more than STARVE_S seconds ago goes first, so none waits forever.
 // A request that arrives while others run therefore starts at once, its
 // kernels overlap those of earlier requests on the device, and finished
 // requests release memory for queued ones.  Every reactor is integrated
@@ -49,6 +53,8 @@ struct Request {
   int32_t* dsteps = nullptr;
   int64_t next = 0;        // first reactor of the next chunk
   int chunks_total = 0, chunks_launched = 0, chunks_done = 0;
+  double step_cost = 0.0;  // FP64 instructions of one step of one reactor
+  std::chrono::steady_clock::time_point admitted;
   int state = Q_QUEUED;
   int err = CK_OK;
   std::string msg;
@@ -76,6 +82,9 @@ bool host_ptr(const void* p) {
 
 size_t per_reactor_bytes(int nn) { return (size_t)nn * 8 + 8 + 8 + 4 + 8; }
 
+// A request admitted longer ago than this is served before shorter ones.
+constexpr double STARVE_S = 30.0;
+
 }  // namespace
 
 struct ck_server {
@@ -90,7 +99,6 @@ struct ck_server {
   std::vector<Request*> active;
   std::unordered_map<uint64_t, Request*> all;
   uint64_t next_ticket = 1;
-  size_t rr = 0;
   bool stop = false;
   std::thread worker;
   int64_t completed = 0;
@@ -155,6 +163,7 @@ void admit(ck_server* s) {
     }
     r->chunks_total = (int)((r->n + s->chunk - 1) / s->chunk);
     r->state = Q_RUNNING;
+    r->admitted = std::chrono::steady_clock::now();
     s->active.push_back(r);
   }
 }
@@ -230,16 +239,24 @@ void dispatcher(ck_server* s) {
       }
       if (r->state == Q_RUNNING && ++r->chunks_done == r->chunks_total) finish_request(s, r);
     }
-    // launch chunks of admitted requests, round-robin
+    // launch chunks: least remaining work first, starving requests before all
+    const auto now = std::chrono::steady_clock::now();
     for (auto& sl : s->slots) {
       if (sl.req) continue;
       Request* pick = nullptr;
-      for (size_t k = 0; k < s->active.size(); ++k) {
-        Request* r = s->active[(s->rr + k) % s->active.size()];
-        if (r->state == Q_RUNNING && r->chunks_launched < r->chunks_total) {
+      bool pick_old = false;
+      double pick_work = 0.0;
+      for (Request* r : s->active) {
+        if (r->state != Q_RUNNING || r->chunks_launched >= r->chunks_total) continue;
+        const bool old = std::chrono::duration<double>(now - r->admitted).count() > STARVE_S;
+        const double work = (double)(r->n - r->next) * r->step_cost;
+        const bool better = !pick || (old && !pick_old) ||
+                            (old == pick_old && (old ? r->admitted < pick->admitted
+                                                     : work < pick_work || (work == pick_work && r->ticket < pick->ticket)));
+        if (better) {
           pick = r;
-          s->rr = (s->rr + k + 1) % s->active.size();
-          break;
+          pick_old = old;
+          pick_work = work;
         }
       }
       if (!pick) break;
@@ -348,6 +365,9 @@ int ck_submit(ck_server* s, const ck_mech* mech, int32_t method, int64_t n, cons
   }
   r->host = h;
   r->bytes = per_reactor_bytes(mech->hm.d.n) * (size_t)n;
+  ck_work_counts wc;
+  ck_count_work(mech, &wc);
+  r->step_cost = method == 0 ? wc.ros4_step_fp64 : wc.rkf45_step_fp64;
   if (r->bytes > s->budget) {
     delete r;
     return srv_fail(CK_AGAIN, "request needs " + std::to_string(per_reactor_bytes(mech->hm.d.n) * n) +
