@@ -134,3 +134,27 @@ def test_loader_validates_new_fields(ck):
     bad["rev"][0] = 2
     with pytest.raises(ck.CKError, match="arrh_rev"):
         ck.load_mechanism(bad)
+
+
+@pytest.mark.parametrize("name,reactor,explicit,n", [("small", 1, False, 64), ("medium", 1, True, 6)])
+def test_fd_jacobian_ros4_on_variants(ck, name, reactor, explicit, n):
+    # the paper's forward-difference ROS4 (Sec. 5) on the Sec. 3 variants
+    m, gm, om = _case(ck, name, reactor, explicit)
+    y, par = _inputs(name, reactor, n, 61)
+    dt = CONFIGS[name]["dt"]
+    yg, stg = _integrate(ck, gm, ORA_ROS4, par, y, dt, jac=1)
+    yo, _, sto, _ = om.integrate(ORA_ROS4, par, y, dt, jac=1)
+    assert np.array_equal(stg, sto) and np.all(stg == 0)
+    assert np.max(np.abs(yg[:, 0] - yo[:, 0]) / yo[:, 0]) <= 1e-6
+    assert np.max(np.abs(yg[:, 1:] - yo[:, 1:])) <= 1e-8
+
+
+@pytest.mark.parametrize("precision", [1, 2])
+def test_precision_form_on_constant_volume(ck, precision):
+    m, gm, om = _case(ck, "medium", 1, False)
+    y, rho = _inputs("medium", 1, 16, 63)
+    yg, stg = _integrate(ck, gm, ORA_ROS4, rho, y, 1e-5, precision=precision)
+    yo, _, sto, _ = om.integrate(ORA_ROS4, rho, y, 1e-5)
+    assert np.array_equal(stg, sto) and np.all(stg == 0)
+    assert np.max(np.abs(yg[:, 0] - yo[:, 0]) / yo[:, 0]) <= 1e-6
+    assert np.max(np.abs(yg[:, 1:] - yo[:, 1:])) <= 1e-8
