@@ -242,18 +242,33 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
   team_species(m, p, y, b, x, false, tab);
   team_sync();
   const int NC = m.n_chunks, CH = m.chunk;
-  for (int c = 0; c < NC; ++c) {
-    const int base = c * CH;
-    for (int li = threadIdx.x; li < CH; li += blockDim.x)
-      if (base + li < m.R) team_reaction(m, m.rxn[base + li], x, b, tab, li, false);
+  if (m.R <= (3 + JP) * CH) {
+    // the right-hand side needs one value per reaction, so the whole chunk
+    // scratch (q, dqT, D, P are contiguous) holds every rate of progress at
+    // once: one reaction pass and one gather, two barriers in all.  The
+    // gather sums in the same order as the chunked form below.
+    for (int i = threadIdx.x; i < m.R; i += blockDim.x) team_reaction(m, m.rxn[i], x, b, tab, i, false);
     team_sync();
     for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
-      const int* cp = m.csr_cptr + k * (NC + 1) + c;
       double w = b.wd[k];
-      for (int e = cp[0]; e < cp[1]; ++e) w = fma(m.csr_nu[e], b.q[m.csr_rx[e] - base], w);
+      for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) w = fma(m.csr_nu[e], b.q[m.csr_rx[e]], w);
       b.wd[k] = w;
     }
     team_sync();
+  } else {
+    for (int c = 0; c < NC; ++c) {
+      const int base = c * CH;
+      for (int li = threadIdx.x; li < CH; li += blockDim.x)
+        if (base + li < m.R) team_reaction(m, m.rxn[base + li], x, b, tab, li, false);
+      team_sync();
+      for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
+        const int* cp = m.csr_cptr + k * (NC + 1) + c;
+        double w = b.wd[k];
+        for (int e = cp[0]; e < cp[1]; ++e) w = fma(m.csr_nu[e], b.q[m.csr_rx[e] - base], w);
+        b.wd[k] = w;
+      }
+      team_sync();
+    }
   }
   const double invrho = 1.0 / x.rho;
   const double cvf = m.cv ? 1.0 : 0.0;  // constant volume: U/RT = H/RT - 1, cv/R = cp/R - 1
