@@ -21,10 +21,14 @@ from . import ck
 DEFAULT_CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "_build", "autotune.json")
 
 
-def mech_digest(m: dict) -> str:
+def mech_digest(m: dict, reactor: int = 0) -> str:
     h = hashlib.sha256()
-    for k in ("mw", "nasa", "tmid", "reac", "prod", "arrh", "rtype", "rev", "arrh0", "eff_ptr", "eff_sp", "eff_val"):
-        h.update(np.ascontiguousarray(m[k]).tobytes())
+    for k in ("mw", "nasa", "tmid", "reac", "prod", "arrh", "rtype", "rev", "arrh0", "eff_ptr", "eff_sp", "eff_val",
+              "arrh_rev"):
+        if k in m:
+            h.update(k.encode())
+            h.update(np.ascontiguousarray(m[k]).tobytes())
+    h.update(str(int(reactor)).encode())
     return h.hexdigest()[:16]
 
 
@@ -53,7 +57,7 @@ def tune(mech, mdict, method, p, y, dt, precision=0, cache=DEFAULT_CACHE, sample
     method, timed on up to `sample` of the given device reactors."""
     import torch
     gpu = torch.cuda.get_device_name()
-    key = f"{mech_digest(mdict)}:{method}:{precision}:{gpu}"
+    key = f"{mech_digest(mdict, getattr(mech, 'reactor', 0))}:{method}:{precision}:{gpu}"
     db = {}
     if os.path.exists(cache):
         try:

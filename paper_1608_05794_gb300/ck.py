@@ -203,6 +203,7 @@ class Mechanism:
         _check(_lib.ck_load_mechanism(C.byref(d), C.byref(h)), "ck_load_mechanism")
         self.h = h
         self.S, self.R, self.n = S, R, S + 1
+        self.reactor = int(reactor)
 
     def close(self):
         if getattr(self, "h", None):
