@@ -309,7 +309,9 @@ int ck_integrate_ros4_noalloc(const ck_mech* mech, int64_t n, const double* p, d
  * 2^x counts 8, the cost of the table-driven evaluation this library uses):
  * one RHS, the Jacobian beyond the RHS it also returns, one LU, one pair of
  * triangular solves, one ROS4 step (Jacobian, 3 RHS, LU, 4 solves, vector
- * work) and one RKF45 step (6 RHS, vector work); exps per RHS; and the
+ * work) and one RKF45 step (6 RHS, vector work); exps per RHS (one per
+ * forward rate, explicit reverse rate and Lindemann k0, and two per species
+ * for the Gibbs factors 2^(+-g_k) that give 1/K_c as a product); and the
  * algorithmic bytes per reactor (state in and out, p, dt, status). */
 typedef struct {
   double rhs_fp64, rhs_exps, jac_fp64, lu_fp64, solve_fp64;
