@@ -73,3 +73,33 @@ def test_molar_masses_must_be_positive():
     m["mw"] = m["mw"].copy()
     m["mw"][1] = -1.0
     _refused(m, "mw must be positive")
+
+
+# argument checks of other entry points that also come before any CUDA call
+CK_EINVAL, CK_ERANGE = 1, 6
+
+
+def test_lu_entry_points_check_their_sizes():
+    L = ck._lib
+    buf = np.zeros(16)
+    ip = np.zeros(16, np.int32)
+    for dim in (0, 129):
+        assert L.ck_lu_factor(1, dim, buf.ctypes.data, ip.ctypes.data, ip.ctypes.data, None) == CK_ERANGE
+        assert L.ck_lu_solve(1, dim, buf.ctypes.data, ip.ctypes.data, buf.ctypes.data, None) == CK_ERANGE
+    assert L.ck_lu_factor(-1, 4, buf.ctypes.data, ip.ctypes.data, ip.ctypes.data, None) == CK_ERANGE
+    assert L.ck_lu_factor(0, 4, None, None, None, None) == 0  # empty batch: nothing to do
+    assert L.ck_lu_factor(1, 4, None, ip.ctypes.data, ip.ctypes.data, None) == CK_EINVAL
+
+
+def test_group_and_server_arguments():
+    import ctypes as C
+    L = ck._lib
+    groups = (ck.Group * 1)()
+    assert L.ck_integrate_groups(5, 1, groups, 0, None) == CK_EINVAL   # method
+    assert L.ck_integrate_groups(0, 0, groups, 0, None) == CK_ERANGE   # n_groups
+    assert L.ck_integrate_groups(0, 17, groups, 0, None) == CK_ERANGE
+    assert L.ck_integrate_groups(0, 1, None, 0, None) == CK_EINVAL
+    out = C.c_void_p()
+    assert L.ck_server_create(0, 4, 0, C.byref(out)) == CK_EINVAL       # budget
+    assert L.ck_server_create(1 << 30, 0, 0, C.byref(out)) == CK_ERANGE  # streams
+    assert L.ck_server_create(1 << 30, 65, 0, C.byref(out)) == CK_ERANGE
