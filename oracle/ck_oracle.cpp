@@ -2,9 +2,13 @@
 //
 // A plain, slow FP64 restatement of Stone, Alferman & Niemeyer, "Accelerating
 // finite-rate chemical kinetics with coprocessors" (arXiv 1608.05794):
-//   * source terms, Sec. 3: Eqs. ydot, tdot, wdot, kfor, krev, kc, tfits;
-//   * analytic Jacobian of that constant-pressure system (the paper recommends
-//     it in Sec. 6; derived here by the chain rule, pinned by complex step);
+//   * source terms, Sec. 3: Eqs. ydot, tdot, wdot, kfor, krev, kc, tfits, at
+//     constant pressure or constant volume (Sec. 3: c_v and u_k), with K_c
+//     or explicit reverse Arrhenius coefficients (Sec. 3);
+//   * analytic Jacobian of that system (the paper recommends it in Sec. 6;
+//     derived here by the chain rule, pinned by complex step), and the
+//     forward-difference Jacobian the paper ran ROS4 with (Sec. 5, CVODE's
+//     difference quotients);
 //   * dense LU with partial pivoting of I/(h gamma) - J (Sec. 2);
 //   * RKF45 (Sec. 2, App. B tableau) and ROS4 in transformed form (Sec. 2,
 //     App. C coefficients);
@@ -12,7 +16,8 @@
 // Where the paper is silent (error norm, step-size update, initial step) the
 // readings are stated at each function.  Nothing here is blocked, fused or
 // reordered for speed.  Only tests/, __graft_entry__.smoke() and bench.py's
-// CPU-baseline leg may load this library; it shares no code with the CUDA path.
+// CPU-baseline and reference legs may load this library; it shares no code
+// with the CUDA path.
 #include "oracle_api.h"
 
 #include <algorithm>
