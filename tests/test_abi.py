@@ -43,3 +43,32 @@ def test_binding_loads_and_reports_version():
     import paper_1608_05794_gb300.ck as ck
     assert "sm_103a" in ck.version()
     assert ck.library_path().endswith("libck.so")
+
+
+def test_header_is_plain_c_and_a_c_program_links(tmp_path):
+    # the boundary is a C ABI: the header compiles as C99, and a C program
+    # links against the library and calls the entry points that need no GPU
+    from paper_1608_05794_gb300.build import build
+    lib = build()
+    src = tmp_path / "use_ck.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include <string.h>
+#include "ck.h"
+int main(void) {
+  ck_solver_opts o;
+  ck_default_opts(&o);
+  if (!(o.rtol == 1e-9 && o.atol == 1e-12 && o.max_steps == 100000 && o.precision == 0 && o.jac == 0)) return 1;
+  if (strcmp(ck_status_str(CK_OK), "ok") != 0) return 2;
+  if (ck_lu_factor(1, 0, 0, 0, 0, 0) != CK_ERANGE) return 3;
+  if (ck_load_mechanism(0, 0) != CK_EINVAL) return 4;
+  printf("%s\n", ck_version());
+  return 0;
+}
+""")
+    exe = tmp_path / "use_ck"
+    subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-I", os.path.join(ROOT, "include"), str(src), lib,
+                    "-Wl,-rpath," + os.path.dirname(lib), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert out.returncode == 0, (out.returncode, out.stderr)
+    assert "sm_103a" in out.stdout
