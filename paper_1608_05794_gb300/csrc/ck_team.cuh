@@ -35,9 +35,11 @@ __device__ __forceinline__ void team_sync() {
 }
 
 // Shared-memory work arrays of one team.
-// Reactions are processed in chunks of m.chunk (the CTA size), so the
-// per-reaction arrays hold one chunk; cs aliases Gp (free once the reaction
-// passes are done).  Gp_k = 2^(g_k) and Gm_k = 2^(-g_k) with g_k = (S/R -
+// The Jacobian processes reactions in chunks of m.chunk (64 if n <= 56, else
+// 256), so the per-reaction arrays hold one chunk; the right-hand side, which
+// keeps one value per reaction, uses them as one array of 10 m.chunk values
+// when all reactions fit.  cs aliases Gp (free once the reaction passes are
+// done).  Gp_k = 2^(g_k) and Gm_k = 2^(-g_k) with g_k = (S/R -
 // H/RT)_k / ln 2, so that 1/K_c of Eq. kc is a product of species factors.
 struct TeamBufs {
   double *X, *Gp, *hRT, *cpR, *Gm, *wd, *aT, *E, *u, *cs;  // [S]
