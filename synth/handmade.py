@@ -77,3 +77,40 @@ def cyclic_network() -> dict:
                 tmid=np.full(4, 1000.0), reac=reac, prod=prod, arrh=arrh, rtype=rtype,
                 rev=np.ones(6, np.uint8), arrh0=arrh0, eff_ptr=eff_ptr, eff_sp=eff_sp,
                 eff_val=eff_val)
+
+
+T_PIN = 1000.0  # K: the temperature the round values of rate_pins() are placed at
+
+
+def rate_pins() -> dict:
+    """Three reactions whose rate coefficients take closed forms (test input).
+
+    Isomers A, B (N1 O1) and dimer D (N2 O2) with constant heat capacities
+    (cp/R = 3.5, 3.5, 7.0, so every ln T term of the Gibbs energies of
+    reaction cancels) and enthalpy / entropy offsets chosen so that, with
+    T0 = T_PIN:
+      A <=> B       k_f = 2 T exp(-T0 ln2 / T)            (A = 2, beta = 1, Ea = R T0 ln 2)
+                    K_c = 3 * 2^(T0/T)                    (dS/R = ln 3, dH/R = -T0 ln 2, dnu = 0)
+      2A (+M) <=> D third body, k_f = 50 (constant),       K_c = 5 R T / p0     (dnu = -1)
+      A + B (+M) <=> D Lindemann, k_inf = 1000, k0 = 10 T^-1 exp(-T0 ln4 / T),
+                    K_c = (5/3) 2^(-T0/T) R T / p0
+    so that at T0: k_f(A<=>B) = T0, K_c = 6; k0 = 10 / (4 T0); and at 2 T0:
+    k_f = 2 sqrt(2) T0, K_c = 3 sqrt(2), k0 the same 10 / (4 T0)."""
+    ln2, ln3, ln5 = np.log(2.0), np.log(3.0), np.log(5.0)
+    R = 8.314462618
+    elem = np.array([[1, 1], [1, 1], [2, 2]], np.int32)  # N O
+    mw = elem.astype(float) @ np.array([14.007e-3, 15.999e-3])
+    nasa = np.zeros((3, 2, 7))
+    a6A, a7A = 1000.0, 20.0
+    nasa[:, :, 0] = np.array([3.5, 3.5, 7.0])[:, None]
+    nasa[:, :, 5] = np.array([a6A, a6A - T_PIN * ln2, 2 * a6A])[:, None]
+    nasa[:, :, 6] = np.array([a7A, a7A + ln3, 2 * a7A + ln5])[:, None]
+    reac = np.array([[0, -1, -1], [0, 0, -1], [0, 1, -1]], np.int32)
+    prod = np.array([[1, -1, -1], [2, -1, -1], [2, -1, -1]], np.int32)
+    arrh = np.array([[2.0, 1.0, R * T_PIN * ln2], [50.0, 0.0, 0.0], [1000.0, 0.0, 0.0]])
+    arrh0 = np.zeros((3, 3))
+    arrh0[2] = [10.0, -1.0, R * T_PIN * 2 * ln2]
+    return dict(names=["A", "B", "D"], elements=["N", "O"], elem=elem, mw=mw, nasa=nasa,
+                tmid=np.full(3, 1000.0), reac=reac, prod=prod, arrh=arrh,
+                rtype=np.array([0, 1, 2], np.uint8), rev=np.ones(3, np.uint8), arrh0=arrh0,
+                eff_ptr=np.zeros(4, np.int32), eff_sp=np.zeros(0, np.int32), eff_val=np.zeros(0))

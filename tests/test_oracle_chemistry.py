@@ -13,14 +13,17 @@ of the oracle's code:
 * the analytic Jacobian against complex-step and central-difference
   derivatives of the right-hand side;
 * LU with partial pivoting against LAPACK;
-* the closed-form A -> B -> C solution through both integrators.
+* the closed-form A -> B -> C solution through both integrators;
+* the rate coefficients themselves (Eqs. kfor, kc, krev and the Lindemann
+  k0) on a hand-built mechanism whose parameters make them round numbers at
+  two temperatures.
 """
 import numpy as np
 import pytest
 
 import synth
 from synth.configs import CONFIGS, load_mechanism
-from synth.handmade import const_cp_species, cyclic_network, linear_chain
+from synth.handmade import T_PIN, const_cp_species, cyclic_network, linear_chain, rate_pins
 from oracle import ORA_RKF45, ORA_ROS4, OracleMech
 
 R_GAS = 8.314462618
@@ -241,3 +244,22 @@ def test_integrated_enthalpy_and_mass(mech_case):
         h1, s1 = hmix(ye[i])
         assert abs(h1 - h0) <= 1e-7 * max(s0, s1)
         assert abs(ye[i, 1:].sum() - 1.0) <= 1e-10
+
+
+def test_rate_coefficients_closed_forms():
+    # rate_pins() places round values at T0 and 2 T0 (derived by hand from the
+    # parameters): a wrong sign of E or of the Gibbs terms, a dropped beta,
+    # p0/RT inverted or the wrong dnu would each move one of them
+    om = OracleMech(rate_pins())
+    T0 = T_PIN
+    p0 = 101325.0
+    for T, kf0, kc0, k0 in ((T0, T0, 6.0, 10.0 / (4.0 * T0)),
+                             (2 * T0, 2.0 * np.sqrt(2.0) * T0, 3.0 * np.sqrt(2.0), 10.0 / (4.0 * T0))):
+        kf, kc, kr, k0s = om.rate_coeffs(T)
+        r = R_GAS * T / p0
+        expect_kf = [kf0, 50.0, 1000.0]
+        expect_kc = [kc0, 5.0 * r, (5.0 / 3.0) * 2.0 ** (-T0 / T) * r]
+        assert kf == pytest.approx(expect_kf, rel=1e-14)
+        assert kc == pytest.approx(expect_kc, rel=1e-13)
+        assert kr == pytest.approx(np.array(expect_kf) / np.array(expect_kc), rel=1e-13)
+        assert k0s[2] == pytest.approx(k0, rel=1e-14) and k0s[0] == 0.0 and k0s[1] == 0.0
