@@ -65,9 +65,15 @@ enum {
   CK_R_BADINPUT = 5   /* non-finite state, T <= 0, p <= 0 or dt < 0 */
 };
 
-/* Limits of this build. */
+/* Limits of this build.  CK_MAX_REACTORS bounds n of every integrating call
+ * (ck_integrate_*, a group of ck_integrate_groups, ck_submit): reactors are
+ * handed out by a 32-bit device work-queue counter that every CTA or thread
+ * advances once past the end, so n + the launch's resident threads must stay
+ * below 2^31.  Larger batches are rejected with CK_ERANGE before anything is
+ * launched; split them into several calls. */
 #define CK_MAX_SPECIES 128
 #define CK_MAX_REACTIONS 32767
+#define CK_MAX_REACTORS (1LL << 30)
 
 typedef struct ck_mech ck_mech;
 
@@ -214,10 +220,16 @@ int ck_integrate_rkf45(const ck_mech* mech, int64_t n, const double* p, double* 
  * `stream`, launched in decreasing order of work_weight (or, when 0, of
  * reactors x the cost of one step of the method from ck_count_work) at full
  * occupancy, so the next group's CTAs take over SMs as the previous group's
- * drain; opts.variant > 0 caps a group's resident CTAs per SM instead.  With use_graph != 0 the fork / kernels / join sequence
- * is captured into a CUDA graph on the first call and replayed on later
- * calls with byte-identical arguments (the cache holds 8 graphs; the input
- * arrays may change contents, not addresses).  Device pointers only. */
+ * drain; opts.variant > 0 caps a group's resident CTAs per SM instead.
+ * flags: CK_GROUPS_SEQUENTIAL launches the groups one after another on
+ * `stream` instead (same order; each then has the whole GPU until its tail);
+ * with CK_GROUPS_GRAPH the fork / kernels / join sequence is captured into a
+ * CUDA graph on the first call and replayed on later calls with
+ * byte-identical arguments and flags (the cache holds 8 graphs; the input
+ * arrays may change contents, not addresses).  Every form gives bitwise the
+ * same results as one ck_integrate_* call per group.  Device pointers only. */
+#define CK_GROUPS_GRAPH 1
+#define CK_GROUPS_SEQUENTIAL 2
 typedef struct {
   const ck_mech* mech;
   int64_t n;
@@ -230,7 +242,7 @@ typedef struct {
   ck_solver_opts opts;
   double work_weight;
 } ck_group;
-int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups, int32_t use_graph,
+int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups, int32_t flags,
                         void* stream);
 /* Free every cached graph (synchronizes the device). */
 int ck_graph_cache_clear(void);
@@ -238,9 +250,13 @@ int ck_graph_cache_clear(void);
 /* ---------------------------------------------------------------- serving
  * A request server for reactor batches that arrive over time (continuous
  * batching; no counterpart in the paper, which integrates one fixed batch).
- * A request is admitted, in arrival order, once its device footprint
- * (n * ((S+1)*8 + 28) bytes: state, p, dt, status, step counts) fits the
- * HBM budget; admitted requests are split into chunks of chunk_reactors
+ * The server's device memory stays within hbm_budget_bytes: at creation each
+ * stream reserves the ROS4 solver scratch of its launches (per-CTA copies of
+ * the Jacobian and the precision form's FP64 iteration matrices; the SM
+ * count x the shared memory of an SM, the most any mechanism can need,
+ * about 35 MB on GB300), and a request is admitted, in arrival order, once
+ * its device footprint (n * ((S+1)*8 + 28) bytes: state, p, dt, status,
+ * step counts) fits in what the reservation leaves; admitted requests are split into chunks of chunk_reactors
  * reactors that a dispatcher thread launches on `streams` CUDA streams, each
  * free stream taking the next chunk of the request with the least estimated
  * remaining work (reactors left x the FP64 cost of one step of its method;
@@ -254,14 +270,18 @@ int ck_graph_cache_clear(void);
 typedef struct ck_server ck_server;
 typedef struct {
   int64_t queued, active, completed;
-  uint64_t bytes_in_use, budget;
+  uint64_t bytes_in_use;  /* reserved scratch + admitted requests */
+  uint64_t budget;
+  uint64_t reserved;      /* solver scratch held by the streams */
 } ck_server_info;
 /* Create a server on the current device.  streams in [1, 64];
- * chunk_reactors <= 0 selects 8192. */
+ * chunk_reactors <= 0 selects 8192.  CK_ERANGE if the budget does not
+ * exceed the streams' reserved scratch. */
 int ck_server_create(size_t hbm_budget_bytes, int32_t streams, int64_t chunk_reactors, ck_server** out);
 /* Queue a request: method 0 ROS4, 1 RKF45; the same arrays and options as
- * ck_integrate_*; steps may be NULL.  *ticket identifies it.  CK_AGAIN if
- * the request alone exceeds the budget. */
+ * ck_integrate_*; steps may be NULL; n in [1, CK_MAX_REACTORS].  *ticket
+ * identifies it.  CK_AGAIN if the request alone exceeds what the budget
+ * leaves beside the reserved scratch. */
 int ck_submit(ck_server* srv, const ck_mech* mech, int32_t method, int64_t n, const double* p, double* y,
               const double* dt, const ck_solver_opts* opts, int32_t* status, int32_t* steps,
               uint64_t* ticket);
@@ -280,26 +300,32 @@ int ck_server_stats(ck_server* srv, ck_server_info* out);
 int ck_server_destroy(ck_server* srv);
 
 /* Allocation-free variant of ck_integrate_ros4 (no counterpart in the paper).
- * Same arguments, arithmetic and results as ck_integrate_ros4, for callers
- * that cannot let a library allocate device memory: a CFD code that hands
- * all device memory to its own pool at start-up and runs with no headroom,
- * or a process under a fixed device-memory budget where an allocation in the
- * middle of a time step could fail.  ck_integrate_ros4 takes its work-queue
- * counter from a per-call stream-ordered allocation; this entry point uses
- * a statically allocated 256-byte device array instead (held on every GPU
- * that loads the library until the process exits) and calls no cudaMalloc,
- * cudaMallocAsync or cudaFree.
+ * Same arguments, arithmetic and results as ck_integrate_ros4 in its FP64
+ * form, for callers that cannot let a library allocate device memory: a CFD
+ * code that hands all device memory to its own pool at start-up and runs
+ * with no headroom, or a process under a fixed device-memory budget where an
+ * allocation in the middle of a time step could fail.  ck_integrate_ros4
+ * takes its work-queue counter and its per-CTA copies of the Jacobian from a
+ * per-call stream-ordered allocation; this entry point uses a statically
+ * allocated 256-byte device array for the counter (held on every GPU that
+ * loads the library until the process exits), keeps no Jacobian copy (a
+ * rejected step recomputes the Jacobian at the unchanged state, which gives
+ * the same values), and calls no cudaMalloc, cudaMallocAsync or cudaFree.
+ *   - Only the FP64 form is available: opts.precision 1 and 2 need per-CTA
+ *     FP64 matrices in device memory and are refused with CK_EINVAL.
  *   - Every array must be a device pointer; host arrays are rejected with
  *     CK_EINVAL because staging them would need device buffers.
  *   - n must not exceed CK_NOALLOC_MAX_REACTORS (CK_ERANGE otherwise).
- *   - The first call on a device looks up the array's device address (once
- *     per device, with that device current); make that first call before
- *     any stream capture.
+ *   - The array's device address is looked up once per device, with that
+ *     device current: ck_load_mechanism does it for the device it loads on
+ *     (so the driver loads the library's device code there, not inside this
+ *     call); a call on a device with no mechanism loaded cannot happen, since
+ *     the handle must belong to the current device.
  *   - All calls on a device share the array: the counter is zeroed on
  *     `stream` before each launch, so calls that overlap on the GPU (on
  *     different streams, or from several host threads) race and must be
  *     serialized by the caller. */
-#define CK_NOALLOC_MAX_REACTORS (1LL << 30)
+#define CK_NOALLOC_MAX_REACTORS CK_MAX_REACTORS
 int ck_integrate_ros4_noalloc(const ck_mech* mech, int64_t n, const double* p, double* y,
                               const double* dt, double* h_inout, const ck_solver_opts* opts,
                               int32_t* steps, int32_t* status, void* stream);
@@ -319,8 +345,32 @@ typedef struct {
   double rhs_bytes, integrate_bytes;
   double ros4_fd_step_fp64;  /* one ROS4 step with the forward-difference Jacobian: S+2 RHS
                                 (f(y) and one per column) + 2 stage RHS, LU, 4 solves, vector work */
+  /* The same work in the flop model of a roofline: an FMA counts 2 flops,
+   * any other FP64 add, multiply, divide or comparison 1; exponentials and
+   * logarithms are not flops and are counted apart as transcendentals (one
+   * ln T and rhs_exps 2^x per RHS).  A ROS4 step that follows a rejected
+   * attempt reuses J and f(y) (the state is unchanged): it costs
+   * ros4_attempt_flops, and a step at a new state ros4_jeval_flops more (the
+   * analytic Jacobian and the RHS it returns; 1 + rhs_exps transcendentals).
+   * Each attempt also evaluates 2 stage RHS (2 (1 + rhs_exps)
+   * transcendentals).  ros4_fd_jeval_flops replaces ros4_jeval_flops with the
+   * forward-difference Jacobian (S+2 RHS). */
+  double rhs_flops, rhs_transc, jac_flops, lu_flops, solve_flops;
+  double ros4_jeval_flops, ros4_attempt_flops, ros4_step_flops, rkf45_step_flops, ros4_fd_jeval_flops;
 } ck_work_counts;
 int ck_count_work(const ck_mech* mech, ck_work_counts* out);
+
+/* Throughput probes of the FP64 pipe, the roofline denominators of the
+ * integrators (no counterpart in the paper).  kind 0: FMA throughput, 8
+ * independent chains a thread over 64 warps an SM; *ops = flops executed (2
+ * per FMA).  kind 1: throughput of this library's table-driven 2^x (the
+ * mechanism's table), 4 independent chains a thread; *ops = exponentials
+ * evaluated (each iteration also takes 2 FP64 adds).  iters in [1, 2^24]
+ * loop iterations a thread; the probe is launched four times on a private
+ * stream, each timed with CUDA events, and *seconds is the fastest of the
+ * last three (the first warms the GPU up).  Synchronizes;
+ * allocates one double a thread of the grid for the probe's results. */
+int ck_probe_fp64(const ck_mech* mech, int32_t kind, int64_t iters, double* seconds, double* ops);
 
 /* Device error word of a mechanism (bit 1: a bounded shared-memory staging
  * wait gave up).  Synchronizes the device; clears the word when reset != 0. */

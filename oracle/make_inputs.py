@@ -1,6 +1,8 @@
 """Write the shaped synthetic mechanisms to ``synth/data`` (TEST INFRASTRUCTURE).
 
-Run once: ``python -m oracle.make_inputs``.  Calls only ``synth`` (random
+Run once: ``python -m oracle.make_inputs`` (``python -m oracle.make_inputs
+explicit_reverse`` writes the explicit-reverse variant of the medium
+mechanism).  Calls only ``synth`` (random
 draws) and ``oracle`` (shaping).  Prints the spectral radius of the analytic
 Jacobian at a few seeded states of each workload as a stiffness report.
 """
@@ -17,7 +19,22 @@ from .mechgen import make_mechanism
 from .oracle import OracleMech
 
 
+def write_explicit_reverse():
+    """The medium mechanism with explicit reverse coefficients on a quarter of
+    its reversible reactions (oracle.mechgen.with_explicit_reverse), stored
+    for the rate-form variant of the benchmark."""
+    from synth.configs import EXPLICIT_REVERSE_MECH, load_mechanism
+    from .mechgen import with_explicit_reverse
+    m = with_explicit_reverse(load_mechanism(CONFIGS["medium"]["mech"]))
+    print(f"  wrote {save_mechanism(EXPLICIT_REVERSE_MECH, m)} ({int((m['rev'] == 2).sum())} explicit reverse)")
+
+
 def main(names=None):
+    if names and "explicit_reverse" in names:
+        write_explicit_reverse()
+        names = [n for n in names if n != "explicit_reverse"]
+        if not names:
+            return
     for cname, cfg in CONFIGS.items():
         if names and cname not in names:
             continue

@@ -1,7 +1,9 @@
 """Launch-shape autotuner for the integrators.
 
 For one (mechanism, method, precision) it times every candidate launch shape
-on a sample of the caller's reactors and keeps the fastest.  The shapes only
+on a sample of the caller's reactors and keeps the fastest; for a mixed
+batch (ck_integrate_groups) it also times the groups side by side against
+one after another and keeps the faster.  The shapes only
 change how reactors are mapped to the GPU (thread per reactor or CTA per
 reactor, the thread grid of a ROS4 team, resident CTAs per SM); every shape
 computes every reactor with the same arithmetic in the same order, so the
@@ -79,6 +81,46 @@ def tune(mech, mdict, method, p, y, dt, precision=0, cache=DEFAULT_CACHE, sample
         timings.append((t, cand))
     best = min(timings, key=lambda x: x[0])[1]
     db[key] = {"opts": best, "timings_s": [[t, c] for t, c in timings], "sample": k}
+    os.makedirs(os.path.dirname(cache), exist_ok=True)
+    tmp = cache + f".tmp{os.getpid()}"
+    with open(tmp, "w") as f:
+        json.dump(db, f, indent=1)
+    os.replace(tmp, cache)
+    return best
+
+
+def tune_groups(method, groups, mdicts, cache=DEFAULT_CACHE, refresh=False):
+    """True when the groups of a ck_integrate_groups call run faster one
+    after another than side by side.  Both launch orders are captured in a
+    CUDA graph, run once and replayed once under timing on the caller's
+    groups (device tensors; every group's y is restored between runs); the
+    two give bitwise the same results.  Cached under the mechanisms' content
+    digests, the group sizes (to the next power of two), the method and the
+    GPU name.  mdicts: the mechanism dict of each group."""
+    import torch
+    gpu = torch.cuda.get_device_name()
+    parts = [f"{mech_digest(md, getattr(g['mech'], 'reactor', 0))}x{1 << max(0, int(g['y'].shape[0] - 1).bit_length())}"
+             for g, md in zip(groups, mdicts)]
+    key = "groups:" + ":".join(parts) + f":{method}:{gpu}"
+    db = {}
+    if os.path.exists(cache):
+        try:
+            db = json.load(open(cache))
+        except (OSError, ValueError):
+            db = {}
+    if key in db and not refresh:
+        return db[key]["sequential"]
+    y0 = [g["y"].clone() for g in groups]
+    times = {}
+    for seq in (False, True):
+        ck.integrate_groups(method, groups, use_graph=True, sequential=seq)  # capture and run
+        for g, y in zip(groups, y0):
+            g["y"].copy_(y)
+        times[seq] = _time(lambda: ck.integrate_groups(method, groups, use_graph=True, sequential=seq), torch)
+        for g, y in zip(groups, y0):
+            g["y"].copy_(y)
+    best = times[True] < times[False]
+    db[key] = {"sequential": best, "timings_s": {"concurrent": times[False], "sequential": times[True]}}
     os.makedirs(os.path.dirname(cache), exist_ok=True)
     tmp = cache + f".tmp{os.getpid()}"
     with open(tmp, "w") as f:

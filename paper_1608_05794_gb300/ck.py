@@ -19,7 +19,8 @@ from .build import LIB, build
 __all__ = [
     "Mechanism", "load_mechanism", "rhs", "jacobian", "lu_factor", "lu_solve", "integrate_ros4",
     "integrate_rkf45", "integrate_ros4_noalloc", "count_work", "Server", "integrate_groups", "Group",
-    "graph_cache_clear", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path",
+    "graph_cache_clear", "device_errors", "SolverOpts", "CKError", "STATUS", "library_path", "probe_fp64",
+    "fp64_peaks",
 ]
 
 STATUS = {0: "OK", 1: "MAXSTEPS", 2: "HMIN", 3: "NONFINITE", 4: "SINGULAR", 5: "BADINPUT"}
@@ -70,12 +71,15 @@ class Group(C.Structure):
 class WorkCounts(C.Structure):
     _fields_ = [(k, C.c_double) for k in ("rhs_fp64", "rhs_exps", "jac_fp64", "lu_fp64", "solve_fp64",
                                            "ros4_step_fp64", "rkf45_step_fp64", "rhs_bytes",
-                                           "integrate_bytes", "ros4_fd_step_fp64")]
+                                           "integrate_bytes", "ros4_fd_step_fp64",
+                                           "rhs_flops", "rhs_transc", "jac_flops", "lu_flops", "solve_flops",
+                                           "ros4_jeval_flops", "ros4_attempt_flops", "ros4_step_flops",
+                                           "rkf45_step_flops", "ros4_fd_jeval_flops")]
 
 
 class ServerInfo(C.Structure):
     _fields_ = [("queued", C.c_int64), ("active", C.c_int64), ("completed", C.c_int64),
-                ("bytes_in_use", C.c_uint64), ("budget", C.c_uint64)]
+                ("bytes_in_use", C.c_uint64), ("budget", C.c_uint64), ("reserved", C.c_uint64)]
 
 
 def _bind():
@@ -104,6 +108,7 @@ def _bind():
     L.ck_server_stats.argtypes = [C.c_void_p, C.POINTER(ServerInfo)]
     L.ck_server_destroy.argtypes = [C.c_void_p]
     L.ck_device_errors.argtypes = [C.c_void_p, C.POINTER(C.c_int32), C.c_int32]
+    L.ck_probe_fp64.argtypes = [C.c_void_p, C.c_int32, C.c_int64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.ck_status_str.restype = C.c_char_p
     L.ck_last_error.restype = C.c_char_p
     L.ck_version.restype = C.c_char_p
@@ -282,9 +287,13 @@ def integrate_ros4_noalloc(mech, p, y, dt, status, h_inout=None, steps=None, opt
                steps, opts, stream)
 
 
-def integrate_groups(method, groups, use_graph=True, stream=None):
+GROUPS_GRAPH, GROUPS_SEQUENTIAL = 1, 2
+
+
+def integrate_groups(method, groups, use_graph=True, stream=None, sequential=False):
     """Integrate several (mech, p, y, dt, status, steps, opts, weight) groups in
-    one call (ck_integrate_groups); device tensors only."""
+    one call (ck_integrate_groups); device tensors only.  sequential: one
+    group after another on the stream instead of side by side."""
     arr = (Group * len(groups))()
     keep = []
     first = None
@@ -299,7 +308,8 @@ def integrate_groups(method, groups, use_graph=True, stream=None):
         g.opts = spec.get("opts") or SolverOpts.make()
         g.work_weight = float(spec.get("weight", 0.0))
         keep.append(spec)
-    _check(_lib.ck_integrate_groups(int(method), len(groups), arr, int(bool(use_graph)), _stream(stream, first)),
+    flags = (GROUPS_GRAPH if use_graph else 0) | (GROUPS_SEQUENTIAL if sequential else 0)
+    _check(_lib.ck_integrate_groups(int(method), len(groups), arr, flags, _stream(stream, first)),
            "ck_integrate_groups")
 
 
@@ -365,6 +375,24 @@ def count_work(mech: Mechanism) -> dict:
     w = WorkCounts()
     _check(_lib.ck_count_work(mech.h, C.byref(w)), "ck_count_work")
     return {k: getattr(w, k) for k, _ in WorkCounts._fields_}
+
+
+def probe_fp64(mech: Mechanism, kind: int, iters: int) -> tuple[float, float]:
+    """(seconds, ops) of an FP64 throughput probe (ck_probe_fp64): kind 0
+    FMA flops, kind 1 the library's 2^x evaluations."""
+    sec, ops = C.c_double(), C.c_double()
+    _check(_lib.ck_probe_fp64(mech.h, int(kind), int(iters), C.byref(sec), C.byref(ops)), "ck_probe_fp64")
+    return sec.value, ops.value
+
+
+def fp64_peaks(mech: Mechanism, iters: int = 10000) -> dict:
+    """Measured FP64 FMA throughput (flop/s) and the cost of one 2^x in
+    flops of FMA-pipe time (w_exp): the roofline denominators."""
+    t_f, f = probe_fp64(mech, 0, iters)
+    t_e, e = probe_fp64(mech, 1, iters // 2)
+    peak = f / t_f
+    w_exp = peak * t_e / e - 2.0  # the probe loop's 2 adds per exponential are not the exponential's
+    return {"fp64_flops_per_s": peak, "exp2_per_s": e / t_e, "w_exp": w_exp, "dfma_s": t_f, "exp2_s": t_e}
 
 
 def device_errors(mech: Mechanism, reset: bool = False) -> int:

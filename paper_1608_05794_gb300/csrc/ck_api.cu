@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -461,6 +462,15 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   hm.n_contrib = (int)con_coef.size();
   hm.csr_nnz = (int)csr_rx.size();
   hm.dev_err = reinterpret_cast<int32_t*>(b + off_err);
+  // resolve the allocation-free entry point's static scratch on this device
+  // now, so that the driver's loading of the library's device code happens
+  // in this call (which allocates anyway) and not in that entry point
+  int32_t* scratch = nullptr;
+  cudaError_t se = ck::noalloc_scratch(&scratch);
+  if (se != cudaSuccess) {
+    ck_free_mechanism(m);
+    return cuda_fail(se, "cudaGetSymbolAddress(allocation-free scratch)");
+  }
   *out = m;
   return CK_OK;
 }
@@ -620,8 +630,8 @@ bool rkf45_team(const ck::HostMech& hm, int form, int64_t n) {
 
 int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* y, const double* dt,
               double* h_io, const ck_solver_opts* opts, int32_t* steps, int32_t* status, void* stream) {
+  if (n < 0 || n > CK_MAX_REACTORS) return fail(CK_ERANGE, "n must be in [0, CK_MAX_REACTORS = 2^30]");
   if (!m) return fail(CK_EINVAL, "mech is NULL");
-  if (n < 0 || n > 0x7fffffffLL) return fail(CK_ERANGE, "n must be in [0, 2^31)");
   if (n == 0) return CK_OK;
   if (!p || !y || !dt || !status) return fail(CK_EINVAL, "p, y, dt and status are required");
   ck_solver_opts o;
@@ -669,7 +679,7 @@ int integrate(int method, const ck_mech* m, int64_t n, const double* p, double* 
   cudaError_t e = cudaMallocAsync(&queue, sizeof(int32_t), st);
   if (e == cudaSuccess) {
     if (method == 0)
-      e = ck::launch_ros4(m->hm, n, dp, dy, ddt, dh, sp, ds, dst, queue, st, cfg);
+      e = ck::launch_ros4(m->hm, n, dp, dy, ddt, dh, sp, ds, dst, queue, st, cfg, nullptr, 0, true);
     else if (rkf45_team(m->hm, o.form, n))
       e = ck::launch_rkf45_team(m->hm, n, dp, dy, ddt, dh, sp, ds, dst, queue, st, cfg);
     else
@@ -721,6 +731,115 @@ double jac_count(const ck::HostMech& hm) {
   c += 3.0 * hm.csr_nnz;      // aT, E, u (wdot is counted in the RHS)
   return c;
 }
+// The same units in the flop model of the roofline (an FMA counts 2 flops,
+// any other FP64 add, multiply, divide or comparison 1; exponentials and
+// logarithms are counted apart, as transcendentals): the algorithm's
+// arithmetic, without the reduction trees, predicated lanes and index work of
+// its GPU mapping.
+struct Ops {
+  double fma = 0, other = 0, transc = 0;
+  double flops() const { return 2.0 * fma + other; }
+};
+
+Ops rhs_ops(const ck::HostMech& hm) {
+  Ops o;
+  const double S = hm.S;
+  const bool cv = hm.d.cv != 0;
+  o.other += cv ? 7 : 9;  // 1/T, log2 T, T^2..T^4, 1/sum(Y/W), rho
+  o.transc += 1;          // ln T
+  o.fma += 16 * S;        // sum Y/W, Gibbs (6), cp (4) and H (5) polynomials
+  o.other += 3 * S;       // [X_k] (2), C (1)
+  o.transc += 2 * S;      // 2^(+-g_k)
+  o.fma += 2 * S;         // cp mixture, sum H wdot
+  o.other += 3 * S + (cv ? 2 * S : 0) + 4;  // Y/W, W/rho, dY/dt; U = H - RT; 1/rho, dT/dt
+  for (const auto& r : hm.rx) {
+    o.fma += 2;           // log2 k_f
+    o.transc += 1;        // k_f
+    o.other += r.nreac - 1;  // forward product
+    if (r.rev == 1) {
+      o.other += (r.nreac + r.nprod) - (r.dnu == 0 ? 1 : 0) + (std::abs((int)r.dnu) == 2 ? 1 : 0) + 1 + (r.nprod - 1);
+      o.other += 1;
+      o.fma += 1;         // q = k_f prod' - k_r prod''
+    } else if (r.rev == 2) {
+      o.fma += 2;
+      o.transc += 1;
+      o.other += (r.nprod - 1) + 1;
+      o.fma += 1;
+    } else {
+      o.other += 1;
+    }
+    if (r.type) {
+      o.fma += r.eff_cnt;  // [M]
+      o.other += 1;        // q = c net
+    }
+    if (r.type == 2) {
+      o.fma += 2;
+      o.transc += 1;
+      o.other += 5;        // k0/k_inf exponent, P_r, 1 + P_r, 1/(1 + P_r), c
+    }
+  }
+  o.fma += hm.csr_nnz;    // wdot_k = sum nu q
+  return o;
+}
+
+Ops jac_ops(const ck::HostMech& hm) {
+  Ops o;
+  const double S = hm.S;
+  o.fma += 4 * S;         // d cp_mix / dT
+  o.other += 4 * S;
+  for (const auto& r : hm.rx) {
+    o.fma += 1;           // d ln k_f / dT
+    o.other += 2;
+    if (r.rev == 1) o.other += r.nreac + r.nprod + 1;      // d ln K_c / dT
+    if (r.rev == 2) {
+      o.fma += 1;
+      o.other += 3;
+    }
+    if (r.type == 2) {
+      o.fma += 1;
+      o.other += 8;       // d ln k0/dT, dc/dT, dc/d[M]
+    }
+    o.other += 2 + (r.type ? 1 : 0);  // c k_f, c k_r, dc/d[M] net
+    o.other += (r.nreac == 2 ? 2 : (r.nreac == 3 ? 6 : 0));
+    if (r.rev) o.other += (r.nprod == 2 ? 2 : (r.nprod == 3 ? 6 : 0));
+    o.fma += r.type ? 2 : 1;  // D (Euler sum)
+    o.other += 3;
+    o.other += 4;             // dq/dT at fixed [X]
+    if (r.type == 2) o.fma += 1;
+    if (!hm.d.cv) o.fma += 1; // at fixed Y
+  }
+  o.fma += hm.n_contrib;        // species block contributions
+  o.fma += 3.0 * hm.csr_nnz;    // d wdot/dT, E, u
+  o.fma += 5 * S;               // column-sum and dense-row terms
+  o.other += 4 * S;
+  o.fma += S * S + S;           // temperature-row column sums
+  o.fma += S * S;               // dense part of the species block
+  o.fma += S;                   // temperature column
+  o.other += 3 * S;
+  o.fma += 2 * S;               // temperature row
+  o.other += 6 * S;
+  o.fma += 2;                   // J_00
+  o.other += 15;
+  return o;
+}
+
+Ops lu_ops(int n) {
+  Ops o;
+  for (int k = 0; k < n; ++k) {
+    const double m = n - k - 1;
+    o.other += 1 + m;       // reciprocal pivot, multipliers
+    o.fma += m * m;         // rank-one update
+  }
+  return o;
+}
+
+Ops solve_ops(int n) {
+  Ops o;
+  o.fma = (double)n * (n - 1);  // forward and back substitution
+  o.other = n;                  // diagonal
+  return o;
+}
+
 double lu_count(int n) {
   double c = 0.0;
   for (int k = 0; k < n; ++k) c += 1 + (n - k - 1) + (double)(n - k - 1) * (n - k - 1);
@@ -746,13 +865,13 @@ int ck_integrate_rkf45(const ck_mech* m, int64_t n, const double* p, double* y, 
 int ck_integrate_ros4_noalloc(const ck_mech* m, int64_t n, const double* p, double* y,
                               const double* dt, double* h_inout, const ck_solver_opts* opts,
                               int32_t* steps, int32_t* status, void* stream) {
-  if (!m) return fail(CK_EINVAL, "mech is NULL");
   if (n < 0) return fail(CK_EINVAL, "n < 0");
   if (n > CK_NOALLOC_MAX_REACTORS)
     return fail(CK_ERANGE, "ck_integrate_ros4_noalloc: n = " + std::to_string(n) +
                                " exceeds CK_NOALLOC_MAX_REACTORS (" +
                                std::to_string((long long)CK_NOALLOC_MAX_REACTORS) +
-                               "); split the batch or use ck_integrate_ros4");
+                               "); split the batch into several calls");
+  if (!m) return fail(CK_EINVAL, "mech is NULL");
   if (n == 0) return CK_OK;
   if (!p || !y || !dt || !status) return fail(CK_EINVAL, "p, y, dt and status are required");
   if (is_host_ptr(p) || is_host_ptr(y) || is_host_ptr(dt) || is_host_ptr(h_inout) ||
@@ -796,6 +915,24 @@ int ck_count_work(const ck_mech* m, ck_work_counts* o) {
                          4.0 * o->solve_fp64 + (double)n * n + 30.0 * n;
   o->rhs_bytes = 8.0 * (2 * n + 1);
   o->integrate_bytes = 8.0 * (2 * n + 2) + 4.0;
+  const Ops rh = rhs_ops(hm), jc = jac_ops(hm), lu = lu_ops(n), so = solve_ops(n);
+  o->rhs_flops = rh.flops();
+  o->rhs_transc = rh.transc;
+  o->jac_flops = jc.flops();
+  o->lu_flops = lu.flops();
+  o->solve_flops = so.flops();
+  // ROS4 attempt: stage vectors, update, error and norm (18 FMAs and 4 other
+  // operations a component) and the diagonal of the iteration matrix
+  const double ros_vec = 2.0 * 18 * n + 4.0 * n + 20;
+  o->ros4_jeval_flops = jc.flops() + rh.flops();
+  o->ros4_attempt_flops = 2.0 * rh.flops() + lu.flops() + 4.0 * so.flops() + ros_vec;
+  o->ros4_step_flops = o->ros4_jeval_flops + o->ros4_attempt_flops;
+  // RKF45 step: six stages, update, error and norm (25 FMAs and 9 other
+  // operations a component)
+  o->rkf45_step_flops = 6.0 * rh.flops() + 2.0 * 25 * n + 9.0 * n + 20;
+  // forward-difference Jacobian: f(y), n columns (each an RHS, a difference
+  // and a quotient a component), the increments and fnorm
+  o->ros4_fd_jeval_flops = (n + 1.0) * rh.flops() + 2.0 * (double)n * n + 8.0 * n;
   return CK_OK;
 }
 

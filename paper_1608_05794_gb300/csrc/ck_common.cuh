@@ -167,6 +167,10 @@ constexpr double RK_D1 = 16.0 / 135.0 - 25.0 / 216.0, RK_D3 = 6656.0 / 12825.0 -
                  RK_D4 = 28561.0 / 56430.0 - 2197.0 / 4104.0, RK_D5 = -9.0 / 50.0 + 1.0 / 5.0,
                  RK_D6 = 2.0 / 55.0;
 
+// Per-CTA global scratch of the ROS4 kernel, in doubles: -J of the current
+// state (n x n) and its diagonal (n).
+__host__ __device__ constexpr size_t ros4_scratch_doubles(int n) { return (size_t)n * n + (size_t)n; }
+
 struct SolverParams {
   double rtol, atol, h0, fixed_h;
   int max_steps;

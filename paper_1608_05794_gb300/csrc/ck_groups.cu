@@ -43,9 +43,9 @@ void destroy(GraphEntry& e) {
   if (e.queues) cudaFree(e.queues);
 }
 
-std::vector<unsigned char> make_key(int method, int ng, const ck_group* g, int device) {
-  std::vector<unsigned char> k(sizeof(int) * 3 + sizeof(ck_group) * ng);
-  int head[3] = {method, ng, device};
+std::vector<unsigned char> make_key(int method, int ng, const ck_group* g, int device, int flags) {
+  std::vector<unsigned char> k(sizeof(int) * 4 + sizeof(ck_group) * ng);
+  int head[4] = {method, ng, device, flags};
   std::memcpy(k.data(), head, sizeof(head));
   std::memcpy(k.data() + sizeof(head), g, sizeof(ck_group) * ng);
   return k;
@@ -68,16 +68,23 @@ cudaError_t launch_group(int method, const ck_group& g, int32_t* queue, cudaStre
   cfg.ctas_per_sm = ctas_per_sm;
   cfg.grid_side = o.team;
   if (method == 0)
-    return ck::launch_ros4(hm, g.n, g.p, g.y, g.dt, g.h_inout, sp, g.steps, g.status, queue, st, cfg);
+    return ck::launch_ros4(hm, g.n, g.p, g.y, g.dt, g.h_inout, sp, g.steps, g.status, queue, st, cfg, nullptr, 0,
+                           true);
   const bool team = o.form == 2 || (o.form == 0 && (hm.S > 32 || g.n < (int64_t)4 * 128 * ck::sm_count()));
   if (team) return ck::launch_rkf45_team(hm, g.n, g.p, g.y, g.dt, g.h_inout, sp, g.steps, g.status, queue, st, cfg);
   return ck::launch_rkf45(hm, g.n, g.p, g.y, g.dt, g.h_inout, sp, g.steps, g.status, queue, st, cfg);
 }
 
 // Record the fork / kernels / join sequence on `st` (captured or not), in
-// the given launch order.
+// the given launch order; sequential: the kernels one after another on `st`.
 cudaError_t record(int method, int ng, const ck_group* g, GraphEntry& e, cudaStream_t st,
-                   const std::vector<int>& caps, const std::vector<int>& order) {
+                   const std::vector<int>& caps, const std::vector<int>& order, bool sequential) {
+  if (sequential) {
+    cudaError_t err = cudaSuccess;
+    for (int k = 0; k < ng && err == cudaSuccess; ++k)
+      err = launch_group(method, g[order[k]], e.queues + order[k], st, caps[order[k]]);
+    return err;
+  }
   cudaError_t err = cudaEventRecord(e.events[0], st);
   for (int k = 0; k < ng && err == cudaSuccess; ++k) {
     const int i = order[k];
@@ -93,17 +100,23 @@ cudaError_t record(int method, int ng, const ck_group* g, GraphEntry& e, cudaStr
 
 extern "C" {
 
-int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups, int32_t use_graph,
+int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups, int32_t flags,
                         void* stream) {
+  const bool use_graph = (flags & CK_GROUPS_GRAPH) != 0;
+  const bool sequential = (flags & CK_GROUPS_SEQUENTIAL) != 0;
+  if (flags & ~(CK_GROUPS_GRAPH | CK_GROUPS_SEQUENTIAL)) return ck::set_error(CK_EINVAL, "unknown flags");
   if (method != 0 && method != 1) return ck::set_error(CK_EINVAL, "method must be 0 (ROS4) or 1 (RKF45)");
   if (n_groups < 1 || n_groups > 16) return ck::set_error(CK_ERANGE, "n_groups must be in [1, 16]");
   if (!groups) return ck::set_error(CK_EINVAL, "groups is NULL");
+  for (int i = 0; i < n_groups; ++i)
+    if (groups[i].n < 1 || groups[i].n > CK_MAX_REACTORS)
+      return ck::set_error(CK_ERANGE, "group " + std::to_string(i) + ": n must be in [1, CK_MAX_REACTORS = 2^30]");
   int dev = 0;
   cudaGetDevice(&dev);
   for (int i = 0; i < n_groups; ++i) {
     const ck_group& g = groups[i];
-    if (!g.mech || g.n < 1 || g.n > 0x7fffffffLL || !g.p || !g.y || !g.dt || !g.status)
-      return ck::set_error(CK_EINVAL, "group " + std::to_string(i) + ": mech, n >= 1, p, y, dt, status required");
+    if (!g.mech || !g.p || !g.y || !g.dt || !g.status)
+      return ck::set_error(CK_EINVAL, "group " + std::to_string(i) + ": mech, p, y, dt, status required");
     if (g.mech->hm.device != dev) return ck::set_error(CK_EINVAL, "group mechanism loaded on another device");
     const ck_solver_opts& o = g.opts;
     if (!(o.rtol > 0.0) || !(o.atol > 0.0) || o.max_steps < 1 || o.precision < 0 || o.precision > 2 ||
@@ -130,7 +143,7 @@ int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups
   }
   std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return w[a] > w[b]; });
   std::lock_guard<std::mutex> lk(g_mu);
-  std::vector<unsigned char> key = make_key(method, n_groups, groups, dev);
+  std::vector<unsigned char> key = make_key(method, n_groups, groups, dev, flags);
   auto it = g_cache.begin();
   for (; it != g_cache.end(); ++it)
     if (it->key == key) break;
@@ -161,7 +174,7 @@ int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups
   GraphEntry& e = g_cache.front();
   cudaError_t err = cudaSuccess;
   if (!use_graph) {
-    err = record(method, n_groups, groups, e, st, caps, order);
+    err = record(method, n_groups, groups, e, st, caps, order, sequential);
   } else {
     if (!e.exec) {
       // capture on a private stream, so the caller's stream may be the legacy default
@@ -169,7 +182,7 @@ int ck_integrate_groups(int32_t method, int32_t n_groups, const ck_group* groups
       err = cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking);
       if (err == cudaSuccess) err = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
       if (err == cudaSuccess) {
-        cudaError_t rec = record(method, n_groups, groups, e, cap, caps, order);
+        cudaError_t rec = record(method, n_groups, groups, e, cap, caps, order, sequential);
         err = cudaStreamEndCapture(cap, &e.graph);
         if (rec != cudaSuccess) err = rec;
       }

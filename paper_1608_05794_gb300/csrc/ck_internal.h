@@ -51,9 +51,17 @@ cudaError_t launch_lu_factor(int64_t batch, int dim, double* a, int32_t* piv, in
                              cudaStream_t st);
 cudaError_t launch_lu_solve(int64_t batch, int dim, const double* lu, const int32_t* piv,
                             double* b, cudaStream_t st);
+// ROS4 over n reactors.  scratch / scratch_bytes: caller-held per-CTA FP64
+// matrices (ros4_scratch_doubles(S+1) doubles a CTA; at most
+// ros4_scratch_bytes_max() bytes for any mechanism); when absent or too
+// small the launch allocates them stream-ordered if may_alloc, and otherwise
+// runs the FP64 form without Jacobian copies (the precision form then fails
+// with cudaErrorNotSupported).
 cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
                         double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
-                        int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);
+                        int32_t* queue, cudaStream_t st, const LaunchCfg& cfg, double* scratch,
+                        size_t scratch_bytes, bool may_alloc);
+size_t ros4_scratch_bytes_max();
 cudaError_t launch_rkf45(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
                          double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
                          int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);

@@ -49,13 +49,15 @@ __device__ __forceinline__ int team_next(int32_t* queue, int* slot) {
 // weights w_i = 1/(atol + rtol |y_i|), fnorm = WRMS_w(f(y)), floor
 // s0 = 1000 |h| U n fnorm (1 when fnorm = 0), and column j =
 // (f(y + s_j e_j) - f(y)) / s_j with s_j = max(sqrt(U) |y_j|, s0 / w_j).
-// f0 = f(y) is computed here and reused as the first stage's f; the n
-// columns cost n team RHS evaluations.  Yt, F: n-vector scratch.
+// f0 = f(y) is computed here (unless have_f0: the caller already holds it
+// for this y) and reused as the first stage's f; the n columns cost n team
+// RHS evaluations.  Yt, F: n-vector scratch.
 static __device__ __noinline__ void team_jacobian_fd(const DevMech& d, const double* tab, double p,
                                                      const double* y, double h, double rtol, double atol,
-                                                     double* f0, double* J, double* Yt, double* F, TeamBufs b) {
+                                                     double* f0, double* J, double* Yt, double* F, TeamBufs b,
+                                                     bool have_f0 = false) {
   const int n = d.n;
-  team_rhs(d, tab, p, y, f0, b);
+  if (!have_f0) team_rhs(d, tab, p, y, f0, b);
   double s = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
     const double v = f0[i] / (atol + rtol * fabs(y[i]));
@@ -126,15 +128,12 @@ __global__ void __launch_bounds__(G * G, 1) k_lu_factor(int64_t batch, int dim, 
   double* A = sm;
   double* invd = A + (size_t)dim * dim;
   int* pv = reinterpret_cast<int*>(invd + dim);
-  double* lb = invd + 2 * dim;
-  double* ub = lb + dim;
-  double* red = ub + dim;
+  double* scratch = invd + 2 * dim;  // lu_scratch_words<G, T>() doubles
   const int64_t nn = (int64_t)dim * dim;
   for (int64_t m = blockIdx.x; m < batch; m += gridDim.x) {
     for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) A[e] = a[m * nn + e];
-    for (int i = threadIdx.x; i < dim; i += blockDim.x) pv[i] = i;
     __syncthreads();
-    const int inf = lu_reg<G, T>(A, dim, pv, invd, lb, ub, red);
+    const int inf = lu_reg<G, T>(A, dim, pv, invd, scratch);
     for (int64_t e = threadIdx.x; e < nn; e += blockDim.x) a[m * nn + e] = A[e];
     for (int i = threadIdx.x; i < dim; i += blockDim.x) piv[m * dim + i] = pv[i];
     if (threadIdx.x == 0) info[m] = inf;
@@ -253,11 +252,31 @@ __device__ void refined_solve(const double* M64, const float* M32, int n, const 
 
 // PREC 0: FP64 LU and solves.  PREC 1 / 2: FP32 LU and solves with one /
 // two steps of FP64 iterative refinement (the rates, K_c, the temperature
-// equation, the error norm and the step control stay FP64).  The precision
-// form keeps its FP64 iteration matrix, which the refinement needs, in
-// m64g[blockIdx.x][n][n] (global memory; 21 MB for 912 CTAs at n = 54, so it
-// stays in L2) and its FP32 factors in the first half of the shared FP64
-// matrix, so both forms need the same shared memory and residency.
+// equation, the error norm and the step control stay FP64).
+//
+// m64g (may be NULL for PREC 0) holds ros4_scratch_doubles(n) doubles per
+// CTA, m64g[blockIdx.x][.]: global memory, 23 KB a CTA at n = 54 (21 MB for
+// the 912 CTAs of the medium workload), so it stays in L2.  Its first n*n
+// doubles hold J of the current state, its last n (precision form) the
+// diagonal J_ii.
+//
+// The matrix factored is A = J - I/(h gamma) = -M rather than the iteration
+// matrix M itself: partial pivoting picks the same rows, the multipliers and
+// the pre-divided upper factor come out identical, and every solve returns
+// exactly -u, so the stage vectors are kept as v_i = -u_i and the method's
+// coefficients enter with their signs flipped.  The results are bitwise those
+// of factoring M, without negating the n^2 entries of each new J.
+//   - After a rejected step (error test, singular matrix or non-finite trial
+//     state) y is unchanged, so J and f(y) are reused rather than recomputed
+//     (only the analytic J: the forward-difference increments depend on h);
+//     the new matrix J - I/(h gamma) is rebuilt from the copy.  With
+//     m64g NULL (the allocation-free entry point) J is recomputed at the same
+//     state instead, which gives the same values.
+//   - The precision form keeps its FP64 iteration matrix, which the
+//     refinement reads, in the first n*n doubles (the diagonal rebuilt from
+//     the last n for each h) and its FP32 factors in the first half of the
+//     shared FP64 matrix, so both forms need the same shared memory and
+//     residency.
 template <int G, int T, int PREC>
 __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_constant__ DevMech d, int64_t N, const double* __restrict__ p,
                                                  double* __restrict__ y, const double* __restrict__ dt,
@@ -278,11 +297,12 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
   double* u4 = u3 + n;
   double* invd = u4 + n;
   int* piv = reinterpret_cast<int*>(invd + n);
-  double* lb = F;   // LU broadcast buffers: F and Yt are free while factoring
-  double* ub = Yt;
+  // the LU's scratch (lu_scratch_words: at most 578 doubles) reuses the
+  // team buffers, free while factoring (9 S + 10 chunk + 48 >= 688 doubles)
   TeamBufs b = carve_bufs(invd + n + (n + 1) / 2, d.S, d.chunk);
   float* M32 = reinterpret_cast<float*>(M);  // PREC >= 1: FP32 factors over the FP64 matrix
-  double* Mg = PREC ? m64g + (size_t)blockIdx.x * n * n : nullptr;
+  double* Mg = m64g ? m64g + (size_t)blockIdx.x * ros4_scratch_doubles(n) : nullptr;
+  const bool keep_j = Mg != nullptr && sp.jac == 0;
   Mix x;
   const bool fixed = sp.fixed_h > 0.0;
   const int tid = threadIdx.x, P = blockDim.x;
@@ -310,29 +330,44 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
       double t = 0.0;
       bool last_rej = false, last_nf = false;
       int sing_run = 0;
+      bool have_j = false;   // J of yv in Mg (analytic form with a copy only)
+      bool have_f = false;   // F0 = f(yv)
       while (t < tf) {
         if (acc + rej >= sp.max_steps) { st = ST_MAXSTEPS; break; }
         const bool clamped = h >= tf - t;
         const double hh = clamped ? tf - t : h;
         if (hh < hmin) { st = last_nf ? ST_NONFINITE : ST_HMIN; break; }
-        // J and f at y; M = I/(hh gamma) - J; LU
-        if (sp.jac == 1) team_jacobian_fd(d, tab, pr, yv, hh, sp.rtol, sp.atol, F0, M, Yt, F, b);
-        else team_jacobian(d, tab, pr, yv, F0, M, b, x);
+        // J and f at y (or the copy kept since a rejected attempt at the
+        // same y); A = J - I/(hh gamma) = -M; LU of A
+        const int nn = n * n;
+        if (!have_j) {
+          if (sp.jac == 1) team_jacobian_fd(d, tab, pr, yv, hh, sp.rtol, sp.atol, F0, M, Yt, F, b, have_f);
+          else team_jacobian(d, tab, pr, yv, F0, M, b, x);
+          team_sync();
+          if (Mg && (keep_j || PREC)) {
+            for (int e = tid; e < nn; e += P) Mg[e] = M[e];
+            if (PREC)
+              for (int i = tid; i < n; i += P) Mg[nn + i] = M[(size_t)i * n + i];
+            __syncthreads();
+          }
+          have_j = keep_j;
+          have_f = true;
+        } else if (PREC == 0) {
+          for (int e = tid; e < nn; e += P) M[e] = Mg[e];
+          team_sync();
+        }
         const double dg = 1.0 / (hh * ROS_GAMMA);
-        for (int e = tid; e < n * n; e += P) M[e] = -M[e];
-        team_sync();
-        for (int i = tid; i < n; i += P) M[(size_t)i * n + i] += dg;
-        team_sync();
         int info;
         if (PREC == 0) {
-          info = lu_reg<G, T, true>(M, n, piv, invd, lb, ub, b.red);
+          for (int i = tid; i < n; i += P) M[(size_t)i * n + i] -= dg;
+          team_sync();
+          info = lu_reg<G, T, true>(M, n, piv, invd, b.X);
         } else {
-          for (int e = tid; e < n * n; e += P) Mg[e] = M[e];
+          for (int i = tid; i < n; i += P) Mg[(size_t)i * n + i] = Mg[nn + i] - dg;
           __syncthreads();
-          for (int e = tid; e < n * n; e += P) M32[e] = (float)Mg[e];
+          for (int e = tid; e < nn; e += P) M32[e] = (float)Mg[e];
           __syncthreads();
-          info = lu_reg<G, T, true>(M32, n, piv, reinterpret_cast<float*>(invd), reinterpret_cast<float*>(lb),
-                              reinterpret_cast<float*>(ub), b.red);
+          info = lu_reg<G, T, true>(M32, n, piv, reinterpret_cast<float*>(invd), reinterpret_cast<float*>(b.X));
         }
         if (info) {
           ++rej;
@@ -343,7 +378,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
         }
         sing_run = 0;
         const double ih = 1.0 / hh;
-        // stage 1: M u1 = f(y)
+        // stage 1: M u1 = f(y), solved as A v1 = f(y) with v = -u (A = -M)
         for (int i = tid; i < n; i += P) u1[i] = F0[i];
         team_sync();
         if (PREC == 0) {
@@ -353,10 +388,10 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
           refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u1, reinterpret_cast<float*>(u4), Yt, PREC);
         }
         // stage 2: M u2 = f(y + a21 u1) + (c21/h) u1
-        for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A21, u1[i], yv[i]);
+        for (int i = tid; i < n; i += P) Yt[i] = fma(-ROS_A21, u1[i], yv[i]);
         team_sync();
         team_rhs(d, tab, pr, Yt, F, b);
-        for (int i = tid; i < n; i += P) u2[i] = fma(ROS_C21 * ih, u1[i], F[i]);
+        for (int i = tid; i < n; i += P) u2[i] = fma(-ROS_C21 * ih, u1[i], F[i]);
         team_sync();
         if (PREC == 0) {
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u2);
@@ -365,11 +400,11 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
           refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u2, reinterpret_cast<float*>(u4), Yt, PREC);
         }
         // stage 3: M u3 = f(y + a31 u1 + a32 u2) + (c31 u1 + c32 u2)/h
-        for (int i = tid; i < n; i += P) Yt[i] = fma(ROS_A32, u2[i], fma(ROS_A31, u1[i], yv[i]));
+        for (int i = tid; i < n; i += P) Yt[i] = fma(-ROS_A32, u2[i], fma(-ROS_A31, u1[i], yv[i]));
         team_sync();
         team_rhs(d, tab, pr, Yt, F, b);
         for (int i = tid; i < n; i += P)
-          u3[i] = fma(ROS_C32 * ih, u2[i], fma(ROS_C31 * ih, u1[i], F[i]));
+          u3[i] = fma(-ROS_C32 * ih, u2[i], fma(-ROS_C31 * ih, u1[i], F[i]));
         team_sync();
         if (PREC == 0) {
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u3);
@@ -379,7 +414,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
         }
         // stage 4: same argument as stage 3 (a4j = a3j, a43 = 0), so f is reused
         for (int i = tid; i < n; i += P)
-          u4[i] = fma(ROS_C43 * ih, u3[i], fma(ROS_C42 * ih, u2[i], fma(ROS_C41 * ih, u1[i], F[i])));
+          u4[i] = fma(-ROS_C43 * ih, u3[i], fma(-ROS_C42 * ih, u2[i], fma(-ROS_C41 * ih, u1[i], F[i])));
         team_sync();
         if (PREC == 0) {
           if (tid < 32) warp_lu_solve<true>(M, n, piv, invd, u4);
@@ -387,13 +422,13 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
         } else {
           refined_solve(Mg, M32, n, piv, reinterpret_cast<const float*>(invd), u4, reinterpret_cast<float*>(F), Yt, PREC);
         }
-        // y* = y + sum m_i u_i (into Yt), e = sum E_i u_i (into F)
+        // y* = y + sum m_i u_i (into Yt), e = sum E_i u_i (into F); u_i = -v_i
         int nf = 0;
         for (int i = tid; i < n; i += P) {
           const double yn =
-              fma(ROS_M4, u4[i], fma(ROS_M3, u3[i], fma(ROS_M2, u2[i], fma(ROS_M1, u1[i], yv[i]))));
+              fma(-ROS_M4, u4[i], fma(-ROS_M3, u3[i], fma(-ROS_M2, u2[i], fma(-ROS_M1, u1[i], yv[i]))));
           Yt[i] = yn;
-          F[i] = fma(ROS_E4, u4[i], fma(ROS_E3, u3[i], fma(ROS_E2, u2[i], ROS_E1 * u1[i])));
+          F[i] = fma(-ROS_E4, u4[i], fma(-ROS_E3, u3[i], fma(-ROS_E2, u2[i], -ROS_E1 * u1[i])));
           nf |= !isfinite(yn);
         }
         nf = __syncthreads_or(nf);
@@ -402,6 +437,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
           team_sync();
           t = clamped ? tf : t + hh;
           ++acc;
+          have_j = have_f = false;
           continue;
         }
         const double e = team_wrms(n, F, yv, Yt, sp.rtol, sp.atol, b.red);
@@ -418,6 +454,7 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
           team_sync();
           t = clamped ? tf : t + hh;
           ++acc;
+          have_j = have_f = false;
           double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(e, -0.25)));
           if (last_rej) fac = fmin(1.0, fac);
           h = hh * fac;
@@ -646,10 +683,10 @@ cudaError_t launch_jacobian_fd(const HostMech& hm, int64_t n, const double* p, c
 cudaError_t launch_lu_factor(int64_t batch, int dim, double* a, int32_t* piv, int32_t* info,
                              cudaStream_t st) {
   if (batch <= 0) return cudaSuccess;
-  const size_t smem = sizeof(double) * ((size_t)dim * dim + 4 * dim + 64);
   LaunchCfg cfg;
   return with_grid(dim, [&](auto Gc, auto Tc) {
     constexpr int G = decltype(Gc)::value, T = decltype(Tc)::value;
+    const size_t smem = sizeof(double) * ((size_t)dim * dim + 2 * dim + lu_scratch_words<G, T>());
     auto kern = k_lu_factor<G, T>;
     const int grid = team_grid(kern, G * G, smem, batch, cfg);
     kern<<<grid, G * G, smem, st>>>(batch, dim, a, piv, info);
@@ -668,9 +705,23 @@ cudaError_t launch_lu_solve(int64_t batch, int dim, const double* lu, const int3
   return cudaGetLastError();
 }
 
+size_t ros4_scratch_bytes_max() {
+  static size_t cached[NOALLOC_MAX_DEVICES] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= NOALLOC_MAX_DEVICES) return 0;
+  if (!cached[dev]) {
+    int smem_sm = 0;
+    cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    // grid * (n^2 + n) * 8 <= grid * (shared memory of a CTA) <= SMs * (shared memory of an SM)
+    cached[dev] = (size_t)sm_count() * (size_t)smem_sm;
+  }
+  return cached[dev];
+}
+
 cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
                         double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
-                        int32_t* queue, cudaStream_t st, const LaunchCfg& cfg) {
+                        int32_t* queue, cudaStream_t st, const LaunchCfg& cfg, double* scratch,
+                        size_t scratch_bytes, bool may_alloc) {
   if (n <= 0) return cudaSuccess;
   const int nn = hm.d.n;
   const size_t smem = ros4_smem_bytes(nn, hm.S, hm.d.chunk);
@@ -680,16 +731,25 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
     constexpr int G = decltype(Gc)::value, T = decltype(Tc)::value;
     auto kern = cfg.precision == 2 ? k_ros4<G, T, 2> : (cfg.precision == 1 ? k_ros4<G, T, 1> : k_ros4<G, T, 0>);
     const int grid = team_grid(kern, G * G, smem, n, cfg);
+    // per-CTA copies of -J (every form) and the FP64 iteration matrices of
+    // the precision form: the caller's scratch when it is large enough, else
+    // a stream-ordered allocation around the launch, else (allocation-free
+    // FP64 form) none
+    const size_t need = sizeof(double) * (size_t)grid * ros4_scratch_doubles(nn);
     double* m64g = nullptr;
-    if (cfg.precision) {
-      // the precision form's per-CTA FP64 matrices, stream-ordered
-      cudaError_t a = cudaMallocAsync(reinterpret_cast<void**>(&m64g),
-                                      sizeof(double) * (size_t)grid * nn * nn, st);
+    bool owned = false;
+    if (scratch && scratch_bytes >= need) {
+      m64g = scratch;
+    } else if (may_alloc) {
+      cudaError_t a = cudaMallocAsync(reinterpret_cast<void**>(&m64g), need, st);
       if (a != cudaSuccess) return a;
+      owned = true;
+    } else if (cfg.precision) {
+      return cudaErrorNotSupported;
     }
     kern<<<grid, G * G, smem, st>>>(hm.d, n, p, y, dt, h_io, sp, steps, status, queue, m64g);
     cudaError_t k = cudaGetLastError();
-    if (m64g) {
+    if (owned) {
       cudaError_t f = cudaFreeAsync(m64g, st);
       if (k == cudaSuccess) k = f;
     }
@@ -749,8 +809,9 @@ cudaError_t launch_ros4_noalloc(const HostMech& hm, int64_t n, const double* p, 
   int32_t* queue = nullptr;
   cudaError_t e = noalloc_scratch(&queue);
   if (e != cudaSuccess) return e;
-  // launch_ros4 zeroes the counter on the stream before the kernel starts
-  return launch_ros4(hm, n, p, y, dt, h_io, sp, steps, status, queue, st, cfg);
+  // launch_ros4 zeroes the counter on the stream before the kernel starts;
+  // no Jacobian copies (a rejected step recomputes J at the same state)
+  return launch_ros4(hm, n, p, y, dt, h_io, sp, steps, status, queue, st, cfg, nullptr, 0, false);
 }
 
 }  // namespace ck

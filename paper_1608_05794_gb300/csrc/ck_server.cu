@@ -67,6 +67,8 @@ struct Slot {
   cudaStream_t stream = nullptr;
   cudaEvent_t ev = nullptr;
   int32_t* queue = nullptr;  // device work-queue counter of this slot
+  double* scratch = nullptr; // ROS4 per-CTA matrices of this slot's launches
+  size_t scratch_bytes = 0;
   Request* req = nullptr;
 };
 
@@ -89,7 +91,7 @@ constexpr double STARVE_S = 30.0;
 
 struct ck_server {
   int device = 0;
-  size_t budget = 0, in_use = 0;
+  size_t budget = 0, in_use = 0, reserved = 0;  // in_use includes the reserved slot scratch
   int64_t chunk = 8192;
   std::vector<Slot> slots;
   std::mutex mu;
@@ -157,6 +159,10 @@ void admit(ck_server* s) {
     }
     if (e == cudaSuccess) e = cudaEventRecord(r->ready, r->home);
     if (e != cudaSuccess) {
+      if (r->block) {
+        cudaFreeAsync(r->block, r->home);
+        r->block = nullptr;
+      }
       s->in_use -= r->bytes;
       fail_req(s, r, CK_ECUDA, std::string("admission: ") + cudaGetErrorString(e));
       continue;
@@ -189,7 +195,8 @@ void launch_chunk(ck_server* s, Slot& sl, Request* r) {
     int32_t* ss = r->dsteps ? r->dsteps + 2 * start : nullptr;
     int32_t* st = r->dst + start;
     if (r->method == 0)
-      e = ck::launch_ros4(hm, cnt, pp, yy, tt, nullptr, sp, ss, st, sl.queue, sl.stream, cfg);
+      e = ck::launch_ros4(hm, cnt, pp, yy, tt, nullptr, sp, ss, st, sl.queue, sl.stream, cfg, sl.scratch,
+                          sl.scratch_bytes, false);
     else if (r->opts.form == 1)
       e = ck::launch_rkf45(hm, cnt, pp, yy, tt, nullptr, sp, ss, st, sl.queue, sl.stream, cfg);
     else
@@ -208,7 +215,10 @@ void finish_request(ck_server* s, Request* r) {
       e = cudaMemcpyAsync(r->status, r->dst, (size_t)r->n * 4, cudaMemcpyDeviceToHost, r->home);
     if (e == cudaSuccess && r->steps)
       e = cudaMemcpyAsync(r->steps, r->dsteps, (size_t)r->n * 8, cudaMemcpyDeviceToHost, r->home);
-    if (e == cudaSuccess) e = cudaFreeAsync(r->block, r->home);
+    if (e == cudaSuccess) {
+      e = cudaFreeAsync(r->block, r->home);
+      r->block = nullptr;
+    }
   }
   if (e == cudaSuccess) e = cudaEventRecord(r->back, r->home);
   if (e != cudaSuccess) {
@@ -282,6 +292,11 @@ void dispatcher(ck_server* s) {
         bool busy = false;
         for (auto& sl : s->slots) busy |= (sl.req == r);
         drop = !busy;
+        if (drop && r->block) {
+          // a failed host request still holds its staging block
+          cudaFreeAsync(r->block, r->home);
+          r->block = nullptr;
+        }
       }
       if (drop) {
         s->in_use -= r->bytes;
@@ -307,8 +322,19 @@ int ck_server_create(size_t hbm_budget_bytes, int32_t streams, int64_t chunk_rea
   *out = nullptr;
   if (hbm_budget_bytes == 0) return srv_fail(CK_EINVAL, "hbm_budget_bytes must be positive");
   if (streams < 1 || streams > 64) return srv_fail(CK_ERANGE, "streams must be in [1, 64]");
+  // every slot holds the ROS4 scratch of its launches for the server's
+  // lifetime (the largest any mechanism can need), inside the budget
+  const size_t per_slot = ck::ros4_scratch_bytes_max();
+  const size_t reserved = per_slot * (size_t)streams;
+  if (per_slot == 0) return srv_fail(CK_ECUDA, "no current CUDA device");
+  if (hbm_budget_bytes <= reserved)
+    return srv_fail(CK_ERANGE, "hbm_budget_bytes must exceed the " + std::to_string(reserved) +
+                                   " bytes of solver scratch that " + std::to_string(streams) +
+                                   " streams reserve (" + std::to_string(per_slot) + " each)");
   ck_server* s = new ck_server;
   s->budget = hbm_budget_bytes;
+  s->reserved = reserved;
+  s->in_use = reserved;
   if (chunk_reactors > 0) s->chunk = chunk_reactors;
   cudaGetDevice(&s->device);
   s->slots.resize(streams);
@@ -316,14 +342,18 @@ int ck_server_create(size_t hbm_budget_bytes, int32_t streams, int64_t chunk_rea
     cudaError_t e = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
     if (e == cudaSuccess) e = cudaMalloc(&sl.queue, sizeof(int32_t));
+    if (e == cudaSuccess) e = cudaMalloc(&sl.scratch, per_slot);
+    sl.scratch_bytes = per_slot;
     if (e != cudaSuccess) {
       for (auto& q : s->slots) {
         if (q.stream) cudaStreamDestroy(q.stream);
         if (q.ev) cudaEventDestroy(q.ev);
         if (q.queue) cudaFree(q.queue);
+        if (q.scratch) cudaFree(q.scratch);
       }
       delete s;
-      return srv_fail(CK_ECUDA, std::string("server streams: ") + cudaGetErrorString(e));
+      return srv_fail(e == cudaErrorMemoryAllocation ? CK_ENOMEM : CK_ECUDA,
+                      std::string("server streams: ") + cudaGetErrorString(e));
     }
   }
   s->worker = std::thread(dispatcher, s);
@@ -334,9 +364,9 @@ int ck_server_create(size_t hbm_budget_bytes, int32_t streams, int64_t chunk_rea
 int ck_submit(ck_server* s, const ck_mech* mech, int32_t method, int64_t n, const double* p, double* y,
               const double* dt, const ck_solver_opts* opts, int32_t* status, int32_t* steps,
               uint64_t* ticket) {
+  if (n < 1 || n > CK_MAX_REACTORS) return srv_fail(CK_ERANGE, "n must be in [1, CK_MAX_REACTORS = 2^30]");
   if (!s || !mech || !ticket) return srv_fail(CK_EINVAL, "server, mech and ticket are required");
   if (method != 0 && method != 1) return srv_fail(CK_EINVAL, "method must be 0 (ROS4) or 1 (RKF45)");
-  if (n < 1 || n > 0x7fffffffLL) return srv_fail(CK_ERANGE, "n must be in [1, 2^31)");
   if (!p || !y || !dt || !status) return srv_fail(CK_EINVAL, "p, y, dt and status are required");
   Request* r = new Request;
   r->mech = mech;
@@ -368,10 +398,10 @@ int ck_submit(ck_server* s, const ck_mech* mech, int32_t method, int64_t n, cons
   ck_work_counts wc;
   ck_count_work(mech, &wc);
   r->step_cost = method == 0 ? wc.ros4_step_fp64 : wc.rkf45_step_fp64;
-  if (r->bytes > s->budget) {
+  if (r->bytes > s->budget - s->reserved) {
     delete r;
     return srv_fail(CK_AGAIN, "request needs " + std::to_string(per_reactor_bytes(mech->hm.d.n) * n) +
-                                  " bytes, more than the server's HBM budget");
+                                  " bytes, more than the server's HBM budget leaves beside its reserved scratch");
   }
   cudaError_t e = cudaStreamCreateWithFlags(&r->home, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaEventCreateWithFlags(&r->ready, cudaEventDisableTiming);
@@ -459,6 +489,7 @@ int ck_server_stats(ck_server* s, ck_server_info* out) {
   out->completed = s->completed;
   out->bytes_in_use = s->in_use;
   out->budget = s->budget;
+  out->reserved = s->reserved;
   return CK_OK;
 }
 
@@ -475,6 +506,7 @@ int ck_server_destroy(ck_server* s) {
     Request* r = kv.second;
     if (r->home) {
       cudaStreamSynchronize(r->home);
+      if (r->block) cudaFree(r->block);
       cudaStreamDestroy(r->home);
     }
     if (r->ready) cudaEventDestroy(r->ready);
@@ -485,6 +517,7 @@ int ck_server_destroy(ck_server* s) {
     cudaStreamDestroy(sl.stream);
     cudaEventDestroy(sl.ev);
     cudaFree(sl.queue);
+    cudaFree(sl.scratch);
   }
   delete s;
   return CK_OK;

@@ -408,21 +408,39 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
 }
 
 // LU with partial pivoting, register-tiled.  The CTA is a G x G grid of
-// threads; thread (tr, tc) holds the elements (tr + G r, tc + G c),
-// r, c < T, of the n x n row-major matrix A (shared memory, n <= G T) in
-// registers.  An FP64 instruction costs a full warp slot of the FP64 pipe
-// however few lanes are active, so every O(n)-per-step part avoids FP64:
-// pivot candidates are compared as integers (the bit pattern of |v| orders
-// like |v|, and NaN sorts above +inf), one thread forms the reciprocal pivot,
-// and one warp scales the multipliers.  Step k: the owners of column k
-// propose candidates, rows k and p are exchanged through shared memory, the
-// multipliers l_i = A_ik / A_kk and the pivot row u_j = A_kj are broadcast
-// through shared memory (lb, ub: n doubles each), and every thread applies
-// A_ij -= l_i u_j to its tile in registers.  On return A holds the unit lower
-// factor below the diagonal and the upper factor on and above it; piv[k] =
-// row exchanged with row k; invd[k] = 1 / U_kk.  Returns 0, or k+1 when pivot
-// k is zero or not finite (the same in every thread).  Ties pick the
-// smallest row index.  red: >= 2 G + G / 2 doubles of shared scratch.
+// threads laid out column-major: thread t = tc G + tr holds the elements
+// (tr + G r, tc + G c), r, c < T, of the n x n row-major matrix A (shared
+// memory, n <= G T) in registers, so the G owners of a matrix column are G
+// consecutive lanes of one warp.  An FP64 instruction costs a full warp slot
+// of the FP64 pipe however few lanes are active, and the non-FP64 work
+// around it sets how densely those slots fill, so step k (slot row and
+// column kq = k / G, position kt = k % G):
+//   1. the owners of column k pick the pivot among rows i >= k (magnitudes
+//      compared as integers: the bit pattern of |v| orders like |v|, NaN
+//      above +inf; ties take the smallest row) with shuffles inside their
+//      group, form 1 / pivot, and write the column below the diagonal, as it
+//      stands after the exchange of rows k and p (row p takes row k's
+//      entry), to lb; their whole warp scales it into the multipliers;
+//   2. barrier; the owners of rows k and p exchange the two rows through
+//      shared memory, which also publishes the new row k (the pivot row) in
+//      ub; barrier;
+//   3. every thread applies A_ij -= l_i u_j to its tile; column k below the
+//      diagonal becomes the multipliers.
+// Two barriers a step.  The slot bounds of a step are compile-time
+// constants (the step is instantiated for every kq), so the update carries
+// no per-element predicates: rows and columns beyond n are zero and lb / ub
+// are zero-padded there, and only slot row and column kq need per-thread
+// tests.  lb is double-buffered because the next pivot's owners write it
+// while other warps may still read the current one.
+// PRE = false: piv[k] receives the row swapped with row k (LAPACK order) and
+// A the factors.  PRE = true (the form the stage solves of ROS4 take): piv
+// receives the composite row permutation (row i of PA is row piv[i] of A),
+// and the strict upper triangle of U is stored pre-divided by its diagonal,
+// so that a solve gathers b once and needs no division in back
+// substitution.  On return A holds the unit lower factor below the diagonal
+// and the upper factor on and above it; invd[k] = 1 / U_kk.  Returns 0, or
+// k+1 when pivot k is zero or not finite (the same in every thread).
+// scratch: lu_scratch_words<G, T>() doubles of shared memory.
 // Bits of |v| as an unsigned integer (orders like |v|; NaN above +inf).
 __device__ __forceinline__ unsigned long long abs_key(double v) {
   return (unsigned long long)__double_as_longlong(v) & 0x7fffffffffffffffULL;
@@ -433,17 +451,162 @@ __device__ __forceinline__ unsigned long long abs_key(float v) {
 __device__ __forceinline__ unsigned long long inf_key(double) { return 0x7ff0000000000000ULL; }
 __device__ __forceinline__ unsigned long long inf_key(float) { return 0x7f800000ULL; }
 
-// PRE = false: piv[k] receives the row swapped with row k (LAPACK order) and
-// A the factors.  PRE = true (the form the stage solves of ROS4 take): piv
-// receives the composite row permutation (row i of PA is row piv[i] of A),
-// and the strict upper triangle of U is stored pre-divided by its diagonal,
-// so that a solve gathers b once and needs no division in back substitution.
-template <int G, int T, bool PRE = false, class F>
-__device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red) {
-  const int tid = threadIdx.x, tr = tid / G, tc = tid - tr * G;
+template <int G, int T>
+__host__ __device__ constexpr int lu_scratch_words() { return 4 * G * T + 2; }
+
+// One pivot step at compile-time slot kq (see lu_reg).  Returns false when
+// the pivot is zero or not finite.
+template <int G, int T, int KQ, bool PRE, class F>
+__device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F* invd, F* scratch) {
+  constexpr int GT = G * T;
+  const int tid = threadIdx.x, tr = tid % G, tc = tid / G, lane = tid & 31;
+  const int k = KQ * G + kt;
+  const int tn = (n + G - 1) / G;  // slots that hold rows / columns below n (warp-uniform)
+  F* lb = scratch + (k & 1) * GT;
+  F* ub = scratch + 2 * GT;
+  F* xb = scratch + 3 * GT;
+  int* sp = reinterpret_cast<int*>(scratch + 4 * GT);
   const unsigned long long INFB = inf_key(F(0));
-  if (PRE)
-    for (int i = tid; i < n; i += blockDim.x) piv[i] = i;
+  // 1. pivot search, reciprocal and multipliers: the warp holding column k
+  const int owner_warp = (kt * G) >> 5;
+  if ((tid >> 5) == owner_warp) {
+    const int base = (kt * G) & 31;  // first lane of the owner group
+    bool sing = false;
+    F ip = F(0);
+    if (tc == kt) {
+      const unsigned gmask = (G >= 32 ? 0xffffffffu : ((1u << G) - 1u)) << base;
+      unsigned long long best = 0;
+      F bv = F(0);
+      int bi = n;
+#pragma unroll
+      for (int r = KQ; r < T; ++r) {
+        if (r >= tn) break;
+        const int i = tr + G * r;
+        const bool ok = (r > KQ || tr >= kt) && i < n;
+        const unsigned long long key = abs_key(a[r][KQ]);
+        if (ok && (bi == n || key > best)) {
+          best = key;
+          bv = a[r][KQ];
+          bi = i;
+        }
+      }
+#pragma unroll
+      for (int off = 1; off < G; off <<= 1) {
+        const unsigned long long ok_ = __shfl_xor_sync(gmask, best, off, G);
+        const F ov = __shfl_xor_sync(gmask, bv, off, G);
+        const int oi = __shfl_xor_sync(gmask, bi, off, G);
+        if (oi < n && (bi == n || ok_ > best || (ok_ == best && oi < bi))) {
+          best = ok_;
+          bv = ov;
+          bi = oi;
+        }
+      }
+      const int p = bi;
+      sing = p >= n || best == 0 || best >= INFB;
+      // column k as it stands after the exchange: row p takes row k's entry
+      const F akk = __shfl_sync(gmask, a[KQ][KQ], kt, G);
+      if (!sing) {
+        ip = F(1) / bv;
+#pragma unroll
+        for (int r = KQ; r < T; ++r) {
+          if (r >= tn) break;
+          const int i = tr + G * r;
+          if (i > k && i < n) lb[i] = (i == p) ? akk : a[r][KQ];
+        }
+      }
+      if (tr == 0) {
+        *sp = sing ? -1 : p;
+        if (!sing) {
+          invd[k] = ip;
+          if (PRE) {
+            const int t = piv[k];
+            piv[k] = piv[p];
+            piv[p] = t;
+          } else {
+            piv[k] = p;
+          }
+        }
+      }
+    }
+    __syncwarp();
+    sing = __shfl_sync(0xffffffffu, (int)sing, base) != 0;
+    ip = __shfl_sync(0xffffffffu, ip, base);
+    if (!sing)
+      for (int i = k + 1 + lane; i < n; i += 32) lb[i] *= ip;
+  }
+  __syncthreads();
+  const int p = *sp;
+  if (p < 0) return false;
+  // 2. exchange rows k and p; the new row k (the pivot row) lands in ub
+  const int pt = p % G, ps = p / G;
+  if (tr == kt) {
+#pragma unroll
+    for (int c = 0; c < T; ++c)
+      if (c < tn) (p != k ? xb : ub)[tc + G * c] = a[KQ][c];
+  }
+  if (p != k && tr == pt) {
+#pragma unroll
+    for (int r = KQ; r < T; ++r)
+      if (r == ps)
+#pragma unroll
+        for (int c = 0; c < T; ++c)
+          if (c < tn) ub[tc + G * c] = a[r][c];
+  }
+  __syncthreads();
+  if (p != k) {
+    if (tr == kt) {
+#pragma unroll
+      for (int c = 0; c < T; ++c)
+        if (c < tn) a[KQ][c] = ub[tc + G * c];
+    }
+    if (tr == pt) {
+#pragma unroll
+      for (int r = KQ; r < T; ++r)
+        if (r == ps)
+#pragma unroll
+          for (int c = 0; c < T; ++c)
+            if (c < tn) a[r][c] = xb[tc + G * c];
+    }
+  }
+  // 3. rank-one update of the trailing tile; column k takes the multipliers.
+  // Slots at or beyond tn hold only padding and are left alone.
+  F u[T];
+#pragma unroll
+  for (int c = KQ; c < T; ++c) u[c] = c < tn ? ub[tc + G * c] : F(0);
+#pragma unroll
+  for (int r = KQ; r < T; ++r) {
+    if (r >= tn) break;
+    const bool live = r > KQ || tr > kt;  // row tr + G r lies below row k
+    const F li = live ? lb[tr + G * r] : F(0);
+#pragma unroll
+    for (int c = KQ + 1; c < T; ++c) {
+      if (c >= tn) break;
+      a[r][c] = fma(-li, u[c], a[r][c]);
+    }
+    if (tc > kt) a[r][KQ] = fma(-li, u[KQ], a[r][KQ]);
+    else if (tc == kt && live) a[r][KQ] = li;
+  }
+  return true;
+}
+
+template <int G, int T, bool PRE, int KQ, class F>
+__device__ __forceinline__ int lu_slots(F (&a)[T][T], int n, int* piv, F* invd, F* scratch) {
+  if constexpr (KQ < T) {
+    for (int kt = 0; kt < G; ++kt) {
+      if (KQ * G + kt >= n) return 0;
+      if (!lu_step<G, T, KQ, PRE>(a, n, kt, piv, invd, scratch)) return KQ * G + kt + 1;
+    }
+    return lu_slots<G, T, PRE, KQ + 1>(a, n, piv, invd, scratch);
+  } else {
+    return 0;
+  }
+}
+
+template <int G, int T, bool PRE = false, class F>
+__device__ int lu_reg(F* A, int n, int* piv, F* invd, F* scratch) {
+  const int tid = threadIdx.x, tr = tid % G, tc = tid / G;
+  for (int e = tid; e < lu_scratch_words<G, T>(); e += blockDim.x) scratch[e] = F(0);
+  for (int i = tid; i < n; i += blockDim.x) piv[i] = i;
   F a[T][T];
 #pragma unroll
   for (int r = 0; r < T; ++r)
@@ -452,135 +615,8 @@ __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* lb, F* ub, double* red)
       const int i = tr + G * r, j = tc + G * c;
       a[r][c] = (i < n && j < n) ? A[i * n + j] : F(0);
     }
-  unsigned long long* rk = reinterpret_cast<unsigned long long*>(red);  // [G] |candidate| bits
-  F* rs = reinterpret_cast<F*>(red + G);                               // [G] signed candidate
-  int* ri = reinterpret_cast<int*>(red + 2 * G);                       // [G] candidate row
-  int info = 0;
-  for (int k = 0; k < n; ++k) {
-    const int kq = k / G, kt = k - kq * G;
-    // 1. candidates from the owners of column k (tc == kt, slot kq)
-    if (tc == kt) {
-      unsigned long long best = 0;
-      F bsig = F(0);
-      int bi = n;
-#pragma unroll
-      for (int c = 0; c < T; ++c) {
-        if (c != kq) continue;
-#pragma unroll
-        for (int r = 0; r < T; ++r) {
-          const int i = tr + G * r;
-          const unsigned long long key = abs_key(a[r][c]);
-          if (i >= k && i < n && (bi == n || key > best)) {
-            best = key;
-            bsig = a[r][c];
-            bi = i;
-          }
-        }
-      }
-      rk[tr] = best;
-      rs[tr] = bsig;
-      ri[tr] = bi;
-    }
-    __syncthreads();
-    unsigned long long best = 0;
-    F pv = F(0);
-    int p = n;
-    for (int t = 0; t < G; ++t) {
-      if (ri[t] >= n) continue;
-      if (p == n || rk[t] > best || (rk[t] == best && ri[t] < p)) {
-        best = rk[t];
-        pv = rs[t];
-        p = ri[t];
-      }
-    }
-    if (p >= n || best == 0 || best >= INFB) {
-      info = k + 1;
-      break;
-    }
-    // 2. row interchange k <-> p
-    const int kt_r = k % G, ks_r = k / G, pt_r = p % G, ps_r = p / G;
-    if (p != k) {
-#pragma unroll
-      for (int r = 0; r < T; ++r) {
-#pragma unroll
-        for (int c = 0; c < T; ++c) {
-          const int j = tc + G * c;
-          if (j < n) {
-            if (tr == kt_r && r == ks_r) ub[j] = a[r][c];
-            if (tr == pt_r && r == ps_r) lb[j] = a[r][c];
-          }
-        }
-      }
-      __syncthreads();
-#pragma unroll
-      for (int r = 0; r < T; ++r) {
-#pragma unroll
-        for (int c = 0; c < T; ++c) {
-          const int j = tc + G * c;
-          if (j < n) {
-            if (tr == kt_r && r == ks_r) a[r][c] = lb[j];
-            if (tr == pt_r && r == ps_r) a[r][c] = ub[j];
-          }
-        }
-      }
-      __syncthreads();
-    }
-    // 3. unscaled column k below the diagonal, the pivot row, the reciprocal
-    if (tid == 0) {
-      if (PRE) {
-        const int t = piv[k];
-        piv[k] = piv[p];
-        piv[p] = t;
-      } else {
-        piv[k] = p;
-      }
-      invd[k] = F(1) / pv;
-    }
-    if (tc == kt) {
-#pragma unroll
-      for (int c = 0; c < T; ++c) {
-        if (c != kq) continue;
-#pragma unroll
-        for (int r = 0; r < T; ++r) {
-          const int i = tr + G * r;
-          if (i > k && i < n) lb[i] = a[r][c];
-        }
-      }
-    }
-    if (tr == kt_r) {
-#pragma unroll
-      for (int r = 0; r < T; ++r) {
-        if (r != ks_r) continue;
-#pragma unroll
-        for (int c = 0; c < T; ++c) {
-          const int j = tc + G * c;
-          if (j > k && j < n) ub[j] = a[r][c];
-        }
-      }
-    }
-    __syncthreads();
-    // one warp scales the multipliers
-    if (tid < 32) {
-      const F ip = invd[k];
-      for (int i = k + 1 + tid; i < n; i += 32) lb[i] *= ip;
-    }
-    __syncthreads();
-    // 4. multipliers into the L factor and rank-one update, in registers
-#pragma unroll
-    for (int r = 0; r < T; ++r) {
-      if (G * r + G - 1 <= k) continue;  // whole slot row above the block
-      const int i = tr + G * r;
-      const bool ri_ok = i > k && i < n;
-      const F li = ri_ok ? lb[i] : F(0);
-#pragma unroll
-      for (int c = 0; c < T; ++c) {
-        if (G * c + G - 1 < k) continue;
-        const int j = tc + G * c;
-        if (ri_ok && j == k) a[r][c] = li;
-        if (ri_ok && j > k && j < n) a[r][c] = fma(-li, ub[j], a[r][c]);
-      }
-    }
-  }
+  __syncthreads();
+  const int info = lu_slots<G, T, PRE, 0>(a, n, piv, invd, scratch);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < T; ++r) {

@@ -58,6 +58,8 @@ def save_mechanism(name: str, m: dict) -> str:
     os.makedirs(DATA_DIR, exist_ok=True)
     path = mechanism_path(name)
     out = {k: m[k] for k in MECH_KEYS}
+    if "arrh_rev" in m:  # explicit reverse Arrhenius coefficients (rev == 2)
+        out["arrh_rev"] = m["arrh_rev"]
     out["names"] = np.array(m["names"], dtype="U16")
     out["elements"] = np.array(m["elements"], dtype="U4")
     np.savez(path, **out)
@@ -84,6 +86,11 @@ def cv_states(cfg_name: str, n: int, seed_offset: int = 0):
     rng = np.random.default_rng(CONFIGS[cfg_name]["state_seed"] + 7000 + seed_offset)
     return y, draw_densities(rng, n)
 
+
+# The medium mechanism with a quarter of its reversible reactions on explicit
+# reverse Arrhenius coefficients (rev == 2, Sec. 3), stored by
+# ``python -m oracle.make_inputs explicit_reverse``.
+EXPLICIT_REVERSE_MECH = "mech_s53_rev"
 
 # Mixed workload: the three mechanisms in one batch (50/35/15 split of
 # 200000 reactors), T U[900, 2800] K, half the reactors of each mechanism

@@ -16,6 +16,7 @@ import numpy as np
 import pytest
 
 from synth.configs import CONFIGS, cv_states, load_mechanism, reactor_states
+from conftest import state_errors
 from oracle import ORA_RKF45, ORA_ROS4, OracleMech
 from oracle.mechgen import with_explicit_reverse
 
@@ -95,16 +96,24 @@ def _integrate(ck, gm, method, par, y, dt, **kw):
     return yd.cpu().numpy(), st.cpu().numpy()
 
 
+def _variant(reactor, explicit):
+    return ("constant volume" if reactor else "constant pressure") + (", explicit reverse" if explicit else "")
+
+
 @pytest.mark.parametrize("method,form", [(ORA_ROS4, 0), (ORA_RKF45, 1), (ORA_RKF45, 2)])
 @pytest.mark.parametrize("name,reactor,explicit,n", [("small", 1, False, 256), ("medium", 1, False, 24),
                                                      ("large", 1, False, 6), ("medium", 0, True, 24),
                                                      ("medium", 1, True, 16)])
-def test_integrate_matches_oracle(ck, method, form, name, reactor, explicit, n):
+def test_integrate_matches_oracle(ck, method, form, name, reactor, explicit, n, parity_report):
     m, gm, om = _case(ck, name, reactor, explicit)
     y, par = _inputs(name, reactor, n, 57)
     dt = CONFIGS[name]["dt"]
     yg, stg = _integrate(ck, gm, method, par, y, dt, form=form)
     yo, _, sto, _ = om.integrate(method, par, y, dt)
+    dTm, dYm = state_errors(yg, yo)
+    parity_report.append({"case": "integrate", "workload": name, "variant": _variant(reactor, explicit),
+                          "form": ("ros4" if method == ORA_ROS4 else f"rkf45 (form={form})"), "reactors": n,
+                          "max_rel_dT": dTm, "max_abs_dY": dYm})
     assert np.array_equal(stg, sto) and np.all(stg == 0)
     assert np.max(np.abs(yg[:, 0] - yo[:, 0]) / yo[:, 0]) <= 1e-6
     assert np.max(np.abs(yg[:, 1:] - yo[:, 1:])) <= 1e-8
@@ -137,24 +146,31 @@ def test_loader_validates_new_fields(ck):
 
 
 @pytest.mark.parametrize("name,reactor,explicit,n", [("small", 1, False, 64), ("medium", 1, True, 6)])
-def test_fd_jacobian_ros4_on_variants(ck, name, reactor, explicit, n):
+def test_fd_jacobian_ros4_on_variants(ck, name, reactor, explicit, n, parity_report):
     # the paper's forward-difference ROS4 (Sec. 5) on the Sec. 3 variants
     m, gm, om = _case(ck, name, reactor, explicit)
     y, par = _inputs(name, reactor, n, 61)
     dt = CONFIGS[name]["dt"]
     yg, stg = _integrate(ck, gm, ORA_ROS4, par, y, dt, jac=1)
     yo, _, sto, _ = om.integrate(ORA_ROS4, par, y, dt, jac=1)
+    dTm, dYm = state_errors(yg, yo)
+    parity_report.append({"case": "integrate", "workload": name, "variant": _variant(reactor, explicit),
+                          "form": "ros4 (jac=1)", "reactors": n, "max_rel_dT": dTm, "max_abs_dY": dYm})
     assert np.array_equal(stg, sto) and np.all(stg == 0)
     assert np.max(np.abs(yg[:, 0] - yo[:, 0]) / yo[:, 0]) <= 1e-6
     assert np.max(np.abs(yg[:, 1:] - yo[:, 1:])) <= 1e-8
 
 
 @pytest.mark.parametrize("precision", [1, 2])
-def test_precision_form_on_constant_volume(ck, precision):
+def test_precision_form_on_constant_volume(ck, precision, parity_report):
     m, gm, om = _case(ck, "medium", 1, False)
     y, rho = _inputs("medium", 1, 16, 63)
     yg, stg = _integrate(ck, gm, ORA_ROS4, rho, y, 1e-5, precision=precision)
     yo, _, sto, _ = om.integrate(ORA_ROS4, rho, y, 1e-5)
+    dTm, dYm = state_errors(yg, yo)
+    parity_report.append({"case": "integrate", "workload": "medium", "variant": "constant volume",
+                          "form": f"ros4 (precision={precision})", "reactors": 16, "max_rel_dT": dTm,
+                          "max_abs_dY": dYm})
     assert np.array_equal(stg, sto) and np.all(stg == 0)
     assert np.max(np.abs(yg[:, 0] - yo[:, 0]) / yo[:, 0]) <= 1e-6
     assert np.max(np.abs(yg[:, 1:] - yo[:, 1:])) <= 1e-8

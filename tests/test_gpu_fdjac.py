@@ -11,6 +11,7 @@ import numpy as np
 import pytest
 
 from synth.configs import CONFIGS, load_mechanism, reactor_states
+from conftest import state_errors
 from oracle import ORA_ROS4, OracleMech
 
 torch = pytest.importorskip("torch")
@@ -92,7 +93,10 @@ def _integrate(ck, gm, p, y, dt, **kw):
     return yd.cpu().numpy(), steps.cpu().numpy(), st.cpu().numpy()
 
 
-def _assert_states_close(y, yo, st, sto):
+def _assert_states_close(y, yo, st, sto, report=None, what=None):
+    if report is not None:
+        dTm, dYm = state_errors(y, yo)
+        report.append(dict(what, max_rel_dT=dTm, max_abs_dY=dYm, statuses_equal=bool(np.array_equal(st, sto))))
     assert np.array_equal(st, sto)
     dT = np.abs(y[:, 0] - yo[:, 0]) / yo[:, 0]
     dY = np.abs(y[:, 1:] - yo[:, 1:])
@@ -101,13 +105,14 @@ def _assert_states_close(y, yo, st, sto):
 
 
 @pytest.mark.parametrize("name,n", [("small", 512), ("medium", 16), ("large", 3)])
-def test_ros4_fd_matches_oracle(ck, name, n):
+def test_ros4_fd_matches_oracle(ck, name, n, parity_report):
     m, gm, om = _mech(ck, name)
     cfg = CONFIGS[name]
     y, p = reactor_states(name, n=n, seed_offset=37)
     yg, sg, stg = _integrate(ck, gm, p, y, cfg["dt"], jac=1)
     yo, so, sto, _ = om.integrate(ORA_ROS4, p, y, cfg["dt"], jac=1)
-    _assert_states_close(yg, yo, stg, sto)
+    _assert_states_close(yg, yo, stg, sto, parity_report,
+                         {"case": "integrate", "workload": name, "form": "ros4 (jac=1)", "reactors": n})
     assert np.all(stg == 0)
     assert np.abs(sg.sum(1) - so.sum(1)).max() <= 0.1 * so.sum(1).max() + 3
 

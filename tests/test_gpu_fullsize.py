@@ -10,6 +10,7 @@ import numpy as np
 import pytest
 
 from synth.configs import CONFIGS, load_mechanism, reactor_states
+from conftest import state_errors
 from oracle import ORA_RKF45, ORA_ROS4, OracleMech
 
 torch = pytest.importorskip("torch")
@@ -35,13 +36,16 @@ def _sample(n, k, seed):
     return np.sort(np.random.default_rng(seed).choice(n, size=k, replace=False))
 
 
-def _assert_states(yg, yo, stg, sto):
+def _assert_states(yg, yo, stg, sto, report=None, what=None):
+    if report is not None:
+        dTm, dYm = state_errors(yg, yo)
+        report.append(dict(what, max_rel_dT=dTm, max_abs_dY=dYm))
     assert np.array_equal(stg, sto)
     assert np.max(np.abs(yg[:, 0] - yo[:, 0]) / yo[:, 0]) <= 1e-6
     assert np.max(np.abs(yg[:, 1:] - yo[:, 1:])) <= 1e-8
 
 
-def test_medium_full_batch_rhs_ros4_rkf45(ck):
+def test_medium_full_batch_rhs_ros4_rkf45(ck, parity_report):
     cfg, m, y, p = _full("medium")
     n = y.shape[0]
     assert n == 131072
@@ -69,25 +73,31 @@ def test_medium_full_batch_rhs_ros4_rkf45(ck):
         assert np.all(stg == 0)
         idx = _sample(n, 24, seed)
         yo, _, sto, _ = om.integrate(method, p[idx], y[idx], cfg["dt"])
-        _assert_states(yg.cpu().numpy()[idx], yo, stg[idx], sto)
+        _assert_states(yg.cpu().numpy()[idx], yo, stg[idx], sto, parity_report,
+                       {"case": "integrate, full batch", "workload": "medium", "reactors": n, "sampled": 24,
+                        "form": "ros4" if method == ORA_ROS4 else "rkf45"})
 
 
-def test_large_full_batch_precision_form(ck):
+def test_large_full_batch_precision_form(ck, parity_report):
     # the precision form (FP32 LU and solves, one FP64 refinement) on the
-    # whole 65536-reactor large batch, against the FP64 oracle
+    # whole 65536-reactor large batch, against the FP64 oracle and beside the
+    # plain FP64 form on the same reactors
     cfg, m, y, p = _full("large")
     n = y.shape[0]
     assert n == 65536
     gm = ck.load_mechanism(m)
     om = OracleMech(m)
-    yg = torch.as_tensor(y, device="cuda")
-    st = torch.empty(n, dtype=torch.int32, device="cuda")
-    ck.integrate_ros4(gm, torch.as_tensor(p, device="cuda"), yg,
-                      torch.full((n,), cfg["dt"], dtype=torch.float64, device="cuda"), st,
-                      opts=ck.SolverOpts.make(precision=1))
-    torch.cuda.synchronize()
-    stg = st.cpu().numpy()
-    assert np.all(stg == 0)
     idx = _sample(n, 8, 74)
     yo, _, sto, _ = om.integrate(ORA_ROS4, p[idx], y[idx], cfg["dt"])
-    _assert_states(yg.cpu().numpy()[idx], yo, stg[idx], sto)
+    for prec in (1, 0):
+        yg = torch.as_tensor(y, device="cuda")
+        st = torch.empty(n, dtype=torch.int32, device="cuda")
+        ck.integrate_ros4(gm, torch.as_tensor(p, device="cuda"), yg,
+                          torch.full((n,), cfg["dt"], dtype=torch.float64, device="cuda"), st,
+                          opts=ck.SolverOpts.make(precision=prec))
+        torch.cuda.synchronize()
+        stg = st.cpu().numpy()
+        assert np.all(stg == 0)
+        _assert_states(yg.cpu().numpy()[idx], yo, stg[idx], sto, parity_report,
+                       {"case": "integrate, full batch", "workload": "large", "reactors": n, "sampled": 8,
+                        "form": f"ros4 (precision={prec})" if prec else "ros4"})

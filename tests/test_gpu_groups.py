@@ -61,3 +61,29 @@ def test_autotuner_picks_a_valid_shape(ck, tmp_path):
     best = autotune.tune(gm, m, 1, _dev(p), _dev(y), _dev(dt), cache=cache, sample=256)
     assert best in autotune.candidates(1, gm.S)
     assert autotune.tune(gm, m, 1, _dev(p), _dev(y), _dev(dt), cache=cache, sample=256) == best  # cached
+
+
+def test_group_order_tuner_picks_and_caches(ck, tmp_path):
+    # concurrent and sequential group launches give the same bits; the tuner
+    # times both and caches its choice
+    from paper_1608_05794_gb300 import autotune
+    groups = mixed_batch(n=300, seed=13)
+    mds = [load_mechanism(CONFIGS[nm]["mech"]) for nm, *_ in groups]
+    specs = [dict(mech=ck.load_mechanism(md), p=_dev(p), y=_dev(y), dt=_dev(dt),
+                  status=torch.empty(len(p), dtype=torch.int32, device="cuda"), opts=ck.SolverOpts.make(form=2))
+             for md, (nm, y, p, dt) in zip(mds, groups)]
+    cache = str(tmp_path / "tune.json")
+    seq = autotune.tune_groups(1, specs, mds, cache=cache)
+    assert isinstance(seq, bool)
+    for sp, (nm, y, p, dt) in zip(specs, groups):
+        assert torch.equal(sp["y"], _dev(y))  # the inputs are restored
+    assert autotune.tune_groups(1, specs, mds, cache=cache) == seq
+    out = []
+    for flag in (False, True):
+        ck.integrate_groups(1, specs, use_graph=True, sequential=flag)
+        torch.cuda.synchronize()
+        out.append([sp["y"].clone() for sp in specs])
+        for sp, (nm, y, p, dt) in zip(specs, groups):
+            sp["y"].copy_(_dev(y))
+    assert all(torch.equal(a, b) for a, b in zip(*out))
+    ck.graph_cache_clear()

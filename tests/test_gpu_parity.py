@@ -15,6 +15,7 @@ import synth
 from synth.configs import CONFIGS, load_mechanism, reactor_states
 from synth.handmade import cyclic_network, linear_chain
 from oracle import ORA_RKF45, ORA_ROS4, OracleMech
+from conftest import plain_relative, state_errors
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -52,21 +53,26 @@ def _gpu_rhs(ck, gm, p, y):
     return out.cpu().numpy()
 
 
-def _assert_rhs_close(f, fo, g):
+def _assert_rhs_close(f, fo, g, report=None, what=None):
     bound = 1e-12 * np.maximum(np.abs(fo), g) + 1e-20
     err = np.abs(f - fo)
+    if report is not None:
+        # the asserted bar scales by the gross rate (cancellation near
+        # equilibrium); the plain relative error with the 1e-20 floor is
+        # reported beside it
+        report.append(dict(what, max_gross_ratio=float(np.max(err / bound)), **plain_relative(err, fo)))
     bad = err > bound
     assert not bad.any(), f"{bad.sum()} entries off; worst ratio {np.max(err / bound):.3g}"
 
 
 @pytest.mark.parametrize("name,n", [("small", 1000), ("medium", 300), ("large", 161)])
-def test_rhs_matches_oracle(ck, name, n):
+def test_rhs_matches_oracle(ck, name, n, parity_report):
     m, gm, om = _mech(ck, name)
     y, p = reactor_states(name, n=n, seed_offset=17)
     f = _gpu_rhs(ck, gm, p, y)
     fo = om.rhs(p, y)
     g = om.rhs_gross(p, y)
-    _assert_rhs_close(f, fo, g)
+    _assert_rhs_close(f, fo, g, parity_report, {"case": "rhs", "workload": name, "reactors": n})
 
 
 def test_rhs_temperature_sweep_crosses_thermo_ranges(ck):
@@ -83,7 +89,7 @@ def test_rhs_temperature_sweep_crosses_thermo_ranges(ck):
 
 
 @pytest.mark.parametrize("name,n", [("small", 70), ("medium", 40), ("large", 9)])
-def test_jacobian_matches_oracle(ck, name, n):
+def test_jacobian_matches_oracle(ck, name, n, parity_report):
     m, gm, om = _mech(ck, name)
     y, p = reactor_states(name, n=n, seed_offset=23)
     nn = y.shape[1]
@@ -94,6 +100,8 @@ def test_jacobian_matches_oracle(ck, name, n):
     Jo, G = om.jacobian(p, y, gross=True)
     bound = 1e-12 * np.maximum(np.abs(Jo), G) + 1e-20
     err = np.abs(J - Jo)
+    parity_report.append(dict(case="jacobian", workload=name, reactors=n, max_gross_ratio=float(np.max(err / bound)),
+                              **plain_relative(err, Jo)))
     assert np.all(err <= bound), f"worst ratio {np.max(err / bound):.3g}"
 
 
@@ -144,7 +152,10 @@ def _integrate_gpu(ck, gm, method, p, y, dt, **kw):
     return yd.cpu().numpy(), steps.cpu().numpy(), st.cpu().numpy(), h.cpu().numpy()
 
 
-def _assert_states_close(y, yo, st, sto):
+def _assert_states_close(y, yo, st, sto, report=None, what=None):
+    if report is not None:
+        dTm, dYm = state_errors(y, yo)
+        report.append(dict(what, max_rel_dT=dTm, max_abs_dY=dYm, statuses_equal=bool(np.array_equal(st, sto))))
     assert np.array_equal(st, sto)
     dT = np.abs(y[:, 0] - yo[:, 0]) / yo[:, 0]
     dY = np.abs(y[:, 1:] - yo[:, 1:])
@@ -155,15 +166,23 @@ def _assert_states_close(y, yo, st, sto):
 FORMS = [(ORA_ROS4, 0), (ORA_RKF45, 1), (ORA_RKF45, 2)]
 
 
+def _form_name(method, **kw):
+    base = "ros4" if method == ORA_ROS4 else "rkf45"
+    tags = [f"{k}={v}" for k, v in sorted(kw.items()) if v]
+    return base + (" (" + ", ".join(tags) + ")" if tags else "")
+
+
 @pytest.mark.parametrize("method,form", FORMS)
-def test_integrate_small_config_full(ck, method, form):
+def test_integrate_small_config_full(ck, method, form, parity_report):
     name = "small"
     m, gm, om = _mech(ck, name)
     cfg = CONFIGS[name]
     y, p = reactor_states(name)
     yg, sg, stg, hg = _integrate_gpu(ck, gm, method, p, y, cfg["dt"], form=form)
     yo, so, sto, ho = om.integrate(method, p, y, cfg["dt"], h_inout=np.zeros(len(p)))
-    _assert_states_close(yg, yo, stg, sto)
+    _assert_states_close(yg, yo, stg, sto, parity_report,
+                         {"case": "integrate", "workload": name, "form": _form_name(method, form=form),
+                          "reactors": len(p)})
     assert np.all(stg == 0)
     # step counts are reported, not required to match
     assert np.abs(sg.sum(1) - so.sum(1)).max() <= 0.1 * so.sum(1).max() + 3
@@ -171,13 +190,15 @@ def test_integrate_small_config_full(ck, method, form):
 
 @pytest.mark.parametrize("method,form", FORMS)
 @pytest.mark.parametrize("name,n", [("medium", 48), ("large", 12)])
-def test_integrate_sampled(ck, method, form, name, n):
+def test_integrate_sampled(ck, method, form, name, n, parity_report):
     m, gm, om = _mech(ck, name)
     cfg = CONFIGS[name]
     y, p = reactor_states(name, n=n, seed_offset=5)
     yg, sg, stg, _ = _integrate_gpu(ck, gm, method, p, y, cfg["dt"], form=form)
     yo, so, sto, _ = om.integrate(method, p, y, cfg["dt"])
-    _assert_states_close(yg, yo, stg, sto)
+    _assert_states_close(yg, yo, stg, sto, parity_report,
+                         {"case": "integrate", "workload": name, "form": _form_name(method, form=form),
+                          "reactors": n})
 
 
 @pytest.mark.parametrize("method", [ORA_ROS4, ORA_RKF45])
@@ -263,11 +284,22 @@ def test_work_counts_scale(ck):
         assert w["lu_fp64"] > n ** 3 / 3
         assert w["ros4_step_fp64"] > w["lu_fp64"] + 3 * w["rhs_fp64"]
         assert w["rhs_exps"] >= len(m["rtype"])
+        # the flop model: LU of an n x n matrix = n reciprocals, n(n-1)/2
+        # multipliers and sum (n-k-1)^2 FMAs (2 flops each) ~ 2n^3/3; a solve
+        # pair n(n-1) FMAs and n products ~ 2n^2
+        assert w["lu_flops"] == n + n * (n - 1) / 2 + 2 * (n - 1) * n * (2 * n - 1) / 6
+        assert w["solve_flops"] == 2 * n * (n - 1) + n
+        assert w["ros4_step_flops"] == w["ros4_jeval_flops"] + w["ros4_attempt_flops"]
+        assert w["ros4_attempt_flops"] > 2 * w["rhs_flops"] + w["lu_flops"] + 4 * w["solve_flops"]
+        assert w["ros4_jeval_flops"] > w["rhs_flops"] + 2 * (n - 1) ** 2  # the species block, twice
+        # one ln T and the exponentials of every RHS
+        assert w["rhs_transc"] == w["rhs_exps"] + 1
+        assert w["rkf45_step_flops"] > 6 * w["rhs_flops"]
 
 
 @pytest.mark.parametrize("precision", [1, 2])
 @pytest.mark.parametrize("name,n", [("small", 128), ("medium", 48), ("large", 16)])
-def test_ros4_precision_form_matches_fp64_oracle(ck, name, n, precision):
+def test_ros4_precision_form_matches_fp64_oracle(ck, name, n, precision, parity_report):
     # FP32 LU and stage solves with one or two FP64 refinement steps per
     # solve; the final states must meet the same bar as the FP64 form
     m, gm, om = _mech(ck, name)
@@ -275,7 +307,9 @@ def test_ros4_precision_form_matches_fp64_oracle(ck, name, n, precision):
     y, p = reactor_states(name, n=n, seed_offset=29)
     yg, sg, stg, _ = _integrate_gpu(ck, gm, ORA_ROS4, p, y, cfg["dt"], precision=precision)
     yo, so, sto, _ = om.integrate(ORA_ROS4, p, y, cfg["dt"])
-    _assert_states_close(yg, yo, stg, sto)
+    _assert_states_close(yg, yo, stg, sto, parity_report,
+                         {"case": "integrate", "workload": name,
+                          "form": _form_name(ORA_ROS4, precision=precision), "reactors": n})
 
 
 def test_precision_option_is_validated(ck):

@@ -103,3 +103,20 @@ def test_group_and_server_arguments():
     assert L.ck_server_create(0, 4, 0, C.byref(out)) == CK_EINVAL       # budget
     assert L.ck_server_create(1 << 30, 0, 0, C.byref(out)) == CK_ERANGE  # streams
     assert L.ck_server_create(1 << 30, 65, 0, C.byref(out)) == CK_ERANGE
+
+
+def test_integrating_entry_points_refuse_batches_beyond_the_queue_limit():
+    # a 32-bit device work queue hands out reactors; n above CK_MAX_REACTORS
+    # (2^30) is refused with CK_ERANGE before any handle or pointer is used
+    import ctypes as C
+    L = ck._lib
+    n = (1 << 31) - 1
+    for fn in (L.ck_integrate_ros4, L.ck_integrate_rkf45, L.ck_integrate_ros4_noalloc):
+        assert fn(None, n, None, None, None, None, None, None, None, None) == CK_ERANGE
+        assert "MAX_REACTORS" in L.ck_last_error().decode()
+        assert fn(None, (1 << 30) + 1, None, None, None, None, None, None, None, None) == CK_ERANGE
+    groups = (ck.Group * 1)()
+    groups[0].n = n
+    assert L.ck_integrate_groups(0, 1, groups, 0, None) == CK_ERANGE
+    t = C.c_uint64()
+    assert L.ck_submit(None, None, 0, n, None, None, None, None, None, None, C.byref(t)) == CK_ERANGE

@@ -5,7 +5,8 @@ allocate device memory, for example a CFD code that gives all device memory
 to its own pool at start-up, or a process held to a fixed memory budget in
 which an allocation in the middle of a time step could fail.  It keeps its
 work-queue counter in a static device array instead of a per-call
-allocation, so its results must equal those of ck_integrate_ros4.  This file
+allocation and keeps no Jacobian copies, so its results must equal those of
+ck_integrate_ros4, and it must draw nothing from the device's memory pool.  This file
 is collected last so that a stop at the first failure has already run every
 other test; it also passes on its own in a fresh process.
 """
@@ -50,6 +51,39 @@ def test_noalloc_matches_regular_entry_point_twice(ck, name, n):
         assert np.max(np.abs(y_na[:, 1:] - ref_y[:, 1:])) <= 1e-8
         assert np.array_equal(steps_na, ref_steps)
     assert np.all(ref_st == 0)
+
+
+def _pool_used_high(reset=False):
+    """High-water mark (bytes) of the current device's default stream-ordered
+    memory pool, which every cudaMallocAsync of the library draws from; read
+    through the driver API.  reset=True zeroes it first."""
+    import ctypes as C
+    cu = C.CDLL("libcuda.so.1")
+    dev = C.c_int()
+    assert cu.cuCtxGetDevice(C.byref(dev)) == 0
+    pool = C.c_void_p()
+    assert cu.cuDeviceGetDefaultMemPool(C.byref(pool), dev) == 0
+    used_mem_high = 8  # CU_MEMPOOL_ATTR_USED_MEM_HIGH
+    v = C.c_uint64(0)
+    if reset:
+        assert cu.cuMemPoolSetAttribute(pool, used_mem_high, C.byref(v)) == 0
+    assert cu.cuMemPoolGetAttribute(pool, used_mem_high, C.byref(v)) == 0
+    return v.value
+
+
+def test_noalloc_takes_no_pool_memory(ck):
+    # the call draws nothing from the stream-ordered pool, while the regular
+    # entry point (work-queue counter, Jacobian copies) does
+    cfg = CONFIGS["medium"]
+    gm = ck.load_mechanism(load_mechanism(cfg["mech"]))
+    y, p = reactor_states("medium", n=64, seed_offset=43)
+    _run(ck, ck.integrate_ros4_noalloc, gm, p, y, cfg["dt"])  # buffers of the helper itself come from torch
+    torch.cuda.synchronize()
+    _pool_used_high(reset=True)
+    _run(ck, ck.integrate_ros4_noalloc, gm, p, y, cfg["dt"])
+    assert _pool_used_high() == 0
+    _run(ck, ck.integrate_ros4, gm, p, y, cfg["dt"])
+    assert _pool_used_high() > 0
 
 
 def test_noalloc_rejects_host_arrays_and_oversize_batches(ck):
