@@ -99,9 +99,13 @@ struct DevMech {
 // T_j = 2^(j/256) from a 256-entry table, 2^r - 1 by its degree-4 Taylor
 // polynomial in r ln 2 (truncation < 4e-17 relative).  The reduction is
 // exact (x - round_{1/256}(x) is representable), so the result is within
-// about one ulp.  |x| > 1000 falls back to the library exp2.
+// about one ulp.  |x| > 1000 (and NaN) falls back to the library exp2, out of
+// line so that the rarely taken branch adds no instructions to the inlined
+// fast path.
+static __device__ __noinline__ double ck_exp2_wide(double x) { return exp2(x); }
+
 __device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ tab) {
-  if (!(fabs(x) <= 1000.0)) return exp2(x);
+  if (!(fabs(x) <= 1000.0)) return ck_exp2_wide(x);
   const double SHIFT = 26388279066624.0;  // 1.5 * 2^44: ulp 2^-8
   double t = x + SHIFT;
   double kx = t - SHIFT;
@@ -119,6 +123,11 @@ __device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ t
   long long b = __double_as_longlong(res) + ((long long)e << 52);
   return __longlong_as_double(b);
 }
+
+// 1 / x rounded to nearest: the value IEEE division 1 / x returns, without
+// the general-division path.
+__device__ __forceinline__ double rcp_rn(double x) { return __drcp_rn(x); }
+__device__ __forceinline__ float rcp_rn(float x) { return __frcp_rn(x); }
 
 // (R T / p0)^dnu for dnu = nprod - nreac in [-2, 2]: the concentration
 // factor of 1/K_c (Eq. kc), by multiplication instead of an exponential.

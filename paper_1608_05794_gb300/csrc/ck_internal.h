@@ -62,6 +62,16 @@ cudaError_t launch_ros4(const HostMech& hm, int64_t n, const double* p, double* 
                         int32_t* queue, cudaStream_t st, const LaunchCfg& cfg, double* scratch,
                         size_t scratch_bytes, bool may_alloc);
 size_t ros4_scratch_bytes_max();
+// launch_ros4 for one team grid (G x G threads, T x T tiles, n <= G T), each
+// in its own translation unit (ck_ros4_GxT.cu).
+#define CK_ROS4_TILE_LAUNCHER(NAME)                                                                          \
+  cudaError_t NAME(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt, double* h_io, \
+                   const SolverParams& sp, int32_t* steps, int32_t* status, int32_t* queue, cudaStream_t st,   \
+                   const LaunchCfg& cfg, double* scratch, size_t scratch_bytes, bool may_alloc);
+CK_ROS4_TILE_LAUNCHER(launch_ros4_8x7)
+CK_ROS4_TILE_LAUNCHER(launch_ros4_16x7)
+CK_ROS4_TILE_LAUNCHER(launch_ros4_16x9)
+#undef CK_ROS4_TILE_LAUNCHER
 cudaError_t launch_rkf45(const HostMech& hm, int64_t n, const double* p, double* y, const double* dt,
                          double* h_io, const SolverParams& sp, int32_t* steps, int32_t* status,
                          int32_t* queue, cudaStream_t st, const LaunchCfg& cfg);

@@ -19,8 +19,7 @@ namespace ck {
 constexpr int PROBE_THREADS = 256;
 constexpr int PROBE_BLOCKS_PER_SM = 8;
 
-__global__ void __launch_bounds__(PROBE_THREADS) k_probe_dfma(int64_t iters, double* out) {
-  const double b = 0.99999999, c = 1e-9;
+__global__ void __launch_bounds__(PROBE_THREADS) k_probe_dfma(int64_t iters, double* out, double b, double c) {
   double a0 = 1e-3 * threadIdx.x, a1 = a0 + 1.0, a2 = a0 + 2.0, a3 = a0 + 3.0;
   double a4 = a0 + 4.0, a5 = a0 + 5.0, a6 = a0 + 6.0, a7 = a0 + 7.0;
   for (int64_t i = 0; i < iters; ++i) {
@@ -82,7 +81,7 @@ extern "C" int ck_probe_fp64(const ck_mech* mech, int32_t kind, int64_t iters, d
   for (int rep = 0; rep < 4 && e == cudaSuccess; ++rep) {  // the first launch warms up
     float ms = 0.0f;
     e = cudaEventRecord(a, st);
-    if (kind == 0) ck::k_probe_dfma<<<blocks, ck::PROBE_THREADS, 0, st>>>(iters, out);
+    if (kind == 0) ck::k_probe_dfma<<<blocks, ck::PROBE_THREADS, 0, st>>>(iters, out, 0.99999999, 1e-9);
     else ck::k_probe_exp2<<<blocks, ck::PROBE_THREADS, 0, st>>>(iters, mech->hm.d.tab, out);
     if (e == cudaSuccess) e = cudaGetLastError();
     if (e == cudaSuccess) e = cudaEventRecord(b, st);

@@ -64,7 +64,7 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
   // the others through red[40..45] across the barriers of the sum below
   double* tf = b.red + 40;
   if (threadIdx.x < 32) {
-    x.invT = 1.0 / x.T;
+    x.invT = rcp_rn(x.T);
     x.lnT = log(x.T);
     x.log2T = x.lnT * INV_LN2;
     x.T2 = x.T * x.T;
@@ -90,7 +90,7 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
     x.T3 = tf[4];
     x.T4 = tf[5];
   }
-  x.Wbar = 1.0 / sumYW;
+  x.Wbar = rcp_rn(sumYW);
   x.rho = m.cv ? p : p / (R_GAS * x.T * sumYW);  // constant volume: p is the density
   double c = 0.0, dcpm = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
@@ -180,7 +180,7 @@ __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r,
       const double l2k0 = fma(-r.E0oR2, x.invT, fma(r.beta0, x.log2T, r.lA02));
       const double k0_kf = ck_exp2(l2k0 - l2kf, tab);
       const double Pr = k0_kf * M;
-      const double inv1p = 1.0 / (1.0 + Pr);
+      const double inv1p = rcp_rn(1.0 + Pr);
       c = Pr * inv1p;
       dcdM = k0_kf * inv1p * inv1p;
       if (want_jac) {
@@ -272,7 +272,7 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
       team_sync();
     }
   }
-  const double invrho = 1.0 / x.rho;
+  const double invrho = rcp_rn(x.rho);
   const double cvf = m.cv ? 1.0 : 0.0;  // constant volume: U/RT = H/RT - 1, cv/R = cp/R - 1
   double cpm = 0.0, hw = 0.0;
   for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
@@ -308,14 +308,13 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
                               double* f, double* J, TeamBufs& b, Mix& x) {
   const int S = m.S, n = m.n;
   team_species(m, p, y, b, x, true, tab);
-  // species block A starts at zero; chunk by chunk, every entry touched by
-  // the chunk adds its fixed-order sum of contributions (one thread per
-  // entry, no conflicts), and every species adds its terms of wdot,
-  // d wdot/dT, E = sum nu D and the dense third-body part u
-  for (int e = threadIdx.x; e < S * S; e += blockDim.x) {
-    const int k = e / S, j = e - k * S;
-    J[(size_t)(1 + k) * n + 1 + j] = 0.0;
-  }
+  // species block A starts at zero (the whole matrix is cleared: the
+  // temperature row and column are written whole further down); chunk by
+  // chunk, every entry touched by the chunk adds its fixed-order sum of
+  // contributions (one thread per entry, no conflicts), and every species
+  // adds its terms of wdot, d wdot/dT, E = sum nu D and the dense
+  // third-body part u
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) J[e] = 0.0;
   team_sync();
   const int NC = m.n_chunks, CH = m.chunk;
   for (int c = 0; c < NC; ++c) {
@@ -351,7 +350,7 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   // d rho/dY (cpf) drops out, and U/RT = H/RT - 1, cv/R = cp/R - 1 take the
   // places of H/RT and cp/R (cvf).  The contributions were pre-scaled by
   // W_k/W_j, so J holds A'_kj = W_k A_kj / W_j here.
-  const double invrho = 1.0 / x.rho;
+  const double invrho = rcp_rn(x.rho);
   const double cvf = m.cv ? 1.0 : 0.0, cpf = 1.0 - cvf;
   double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = x.dcpm, cw = 0.0, ha = 0.0, eu = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
@@ -385,15 +384,25 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   }
   team_sync();
   // species block (J_kj = A'_kj + dense_k / W_j) and temperature column
-  const int SS = S * S;
-  for (int e = threadIdx.x; e < SS; e += blockDim.x) {
-    const int k = e / S, j = e - k * S;
-    double* a = J + (size_t)(1 + k) * n + 1 + j;
-    *a = fma(b.u[k], m.invW[j], *a);
+  // entries e = k S + j of the species block, (k, j) advanced without
+  // dividing by the runtime S
+  {
+    const int P = blockDim.x, dk = P / S, dj = P - (P / S) * S;
+    int k = threadIdx.x / S, j = threadIdx.x - k * S;
+    for (; k < S;) {
+      double* a = J + (size_t)(1 + k) * n + 1 + j;
+      *a = fma(b.u[k], m.invW[j], *a);
+      k += dk;
+      j += dj;
+      if (j >= S) {
+        j -= S;
+        ++k;
+      }
+    }
   }
   for (int k = threadIdx.x; k < S; k += blockDim.x)
     J[(size_t)(1 + k) * n] = m.W[k] * invrho * fma(cpf * b.wd[k], x.invT, b.aT[k]);
-  const double inv_cpm = 1.0 / cpm;
+  const double inv_cpm = rcp_rn(cpm);
   const double inv_rc = invrho * inv_cpm;
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
     const double t1 = x.T * (x.rho * b.cs[j] - cpf * x.Wbar * he) * inv_rc;
@@ -454,14 +463,46 @@ __device__ __forceinline__ unsigned long long inf_key(float) { return 0x7f800000
 template <int G, int T>
 __host__ __device__ constexpr int lu_scratch_words() { return 4 * G * T + 2; }
 
+
+// Slot row ps (>= KQ; the same in every thread) of a tile out to / in from
+// a shared row buffer.  The switch is on a CTA-uniform value, so only the
+// taken case executes, instead of a predicated copy of every slot row.
+template <int G, int T, int KQ, class F>
+__device__ __forceinline__ void lu_slot_row_out(const F (&a)[T][T], int ps, int tn, F* row) {
+  const int tc = threadIdx.x / G;
+  if constexpr (KQ < T) {
+    if (ps == KQ) {
+#pragma unroll
+      for (int c = 0; c < T; ++c)
+        if (c < tn) row[tc + G * c] = a[KQ][c];
+    } else {
+      lu_slot_row_out<G, T, KQ + 1>(a, ps, tn, row);
+    }
+  }
+}
+template <int G, int T, int KQ, class F>
+__device__ __forceinline__ void lu_slot_row_in(F (&a)[T][T], int ps, int tn, const F* row) {
+  const int tc = threadIdx.x / G;
+  if constexpr (KQ < T) {
+    if (ps == KQ) {
+#pragma unroll
+      for (int c = 0; c < T; ++c)
+        if (c < tn) a[KQ][c] = row[tc + G * c];
+    } else {
+      lu_slot_row_in<G, T, KQ + 1>(a, ps, tn, row);
+    }
+  }
+}
+
 // One pivot step at compile-time slot kq (see lu_reg).  Returns false when
 // the pivot is zero or not finite.
-template <int G, int T, int KQ, bool PRE, class F>
+template <int G, int T, int KQ, bool PRE, bool FULL, class F>
 __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F* invd, F* scratch) {
   constexpr int GT = G * T;
   const int tid = threadIdx.x, tr = tid % G, tc = tid / G, lane = tid & 31;
   const int k = KQ * G + kt;
-  const int tn = (n + G - 1) / G;  // slots that hold rows / columns below n (warp-uniform)
+  // slots that hold rows / columns below n (warp-uniform); FULL: all T
+  const int tn = FULL ? T : (n + G - 1) / G;
   F* lb = scratch + (k & 1) * GT;
   F* ub = scratch + 2 * GT;
   F* xb = scratch + 3 * GT;
@@ -506,7 +547,7 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
       // column k as it stands after the exchange: row p takes row k's entry
       const F akk = __shfl_sync(gmask, a[KQ][KQ], kt, G);
       if (!sing) {
-        ip = F(1) / bv;
+        ip = rcp_rn(bv);
 #pragma unroll
         for (int r = KQ; r < T; ++r) {
           if (r >= tn) break;
@@ -544,14 +585,7 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
     for (int c = 0; c < T; ++c)
       if (c < tn) (p != k ? xb : ub)[tc + G * c] = a[KQ][c];
   }
-  if (p != k && tr == pt) {
-#pragma unroll
-    for (int r = KQ; r < T; ++r)
-      if (r == ps)
-#pragma unroll
-        for (int c = 0; c < T; ++c)
-          if (c < tn) ub[tc + G * c] = a[r][c];
-  }
+  if (p != k && tr == pt) lu_slot_row_out<G, T, KQ>(a, ps, tn, ub);
   __syncthreads();
   if (p != k) {
     if (tr == kt) {
@@ -559,14 +593,7 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
       for (int c = 0; c < T; ++c)
         if (c < tn) a[KQ][c] = ub[tc + G * c];
     }
-    if (tr == pt) {
-#pragma unroll
-      for (int r = KQ; r < T; ++r)
-        if (r == ps)
-#pragma unroll
-          for (int c = 0; c < T; ++c)
-            if (c < tn) a[r][c] = xb[tc + G * c];
-    }
+    if (tr == pt) lu_slot_row_in<G, T, KQ>(a, ps, tn, xb);
   }
   // 3. rank-one update of the trailing tile; column k takes the multipliers.
   // Slots at or beyond tn hold only padding and are left alone.
@@ -589,14 +616,14 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
   return true;
 }
 
-template <int G, int T, bool PRE, int KQ, class F>
+template <int G, int T, bool PRE, bool FULL, int KQ, class F>
 __device__ __forceinline__ int lu_slots(F (&a)[T][T], int n, int* piv, F* invd, F* scratch) {
   if constexpr (KQ < T) {
     for (int kt = 0; kt < G; ++kt) {
       if (KQ * G + kt >= n) return 0;
-      if (!lu_step<G, T, KQ, PRE>(a, n, kt, piv, invd, scratch)) return KQ * G + kt + 1;
+      if (!lu_step<G, T, KQ, PRE, FULL>(a, n, kt, piv, invd, scratch)) return KQ * G + kt + 1;
     }
-    return lu_slots<G, T, PRE, KQ + 1>(a, n, piv, invd, scratch);
+    return lu_slots<G, T, PRE, FULL, KQ + 1>(a, n, piv, invd, scratch);
   } else {
     return 0;
   }
@@ -616,7 +643,10 @@ __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* scratch) {
       a[r][c] = (i < n && j < n) ? A[i * n + j] : F(0);
     }
   __syncthreads();
-  const int info = lu_slots<G, T, PRE, 0>(a, n, piv, invd, scratch);
+  // every slot holds real rows and columns (n > G (T - 1)): the steps need no
+  // run-time slot bound
+  const int info = (n > G * (T - 1)) ? lu_slots<G, T, PRE, true, 0>(a, n, piv, invd, scratch)
+                                     : lu_slots<G, T, PRE, false, 0>(a, n, piv, invd, scratch);
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < T; ++r) {

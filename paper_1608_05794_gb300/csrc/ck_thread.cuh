@@ -39,7 +39,7 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
                                            double* f, int fs, double* X, double* G, double* wd) {
   const int S = m.S;
   const double T = y[0];
-  const double invT = 1.0 / T;
+  const double invT = __drcp_rn(T);
   const double lnT = log(T);
   const double log2T = lnT * INV_LN2;
   const double T2 = T * T, T3 = T2 * T, T4 = T3 * T;
@@ -110,7 +110,7 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
     if (r.nprod > 1) wd[r.sp[4]] += q;
     if (r.nprod > 2) wd[r.sp[5]] += q;
   }
-  const double invrho = 1.0 / rho;
+  const double invrho = __drcp_rn(rho);
   const double cvf = m.cv ? 1.0 : 0.0;
   double cpm = 0.0, hw = 0.0;
   for (int k = 0; k < S; ++k) {
