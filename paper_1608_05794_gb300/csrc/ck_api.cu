@@ -315,8 +315,9 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   // Jacobian contributions, chunk by chunk: A[k][j] += nu_ki * P[i][slot] for
   // every slot of reaction i holding species j (and nu_ki (eff_ij - 1) *
   // P[i][6] for the third-body corrections), grouped by entry (k, j)
-  std::vector<int32_t> jc_ptr(1, 0), jc_idx, jc_cp(1, 0), con_pidx;
-  std::vector<double> con_coef;
+  std::vector<int32_t> jc_ptr(1, 0);
+  std::vector<JcEntry> jc;
+  std::vector<JcTerm> jt;
   for (int c = 0; c < n_chunks; ++c) {
     std::vector<std::vector<std::pair<double, int32_t>>> ent((size_t)S * S);
     for (int k = 0; k < S; ++k) {
@@ -347,14 +348,19 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
                      [&](int a, int b) { return ent[a].size() > ent[b].size(); });
     for (int e : order_e) {
       const int k = e / S, j = e % S;
-      jc_idx.push_back((1 + k) * (S + 1) + 1 + j);
+      JcEntry h{};
+      h.idx = (1 + k) * (S + 1) + 1 + j;
+      h.beg = (int32_t)jt.size();
       for (auto& cc : ent[e]) {
-        con_coef.push_back(cc.first);
-        con_pidx.push_back(cc.second);
+        JcTerm t{};
+        t.coef = cc.first;
+        t.pidx = cc.second;
+        jt.push_back(t);
       }
-      jc_cp.push_back((int32_t)con_coef.size());
+      h.end = (int32_t)jt.size();
+      jc.push_back(h);
     }
-    jc_ptr.push_back((int32_t)jc_idx.size());
+    jc_ptr.push_back((int32_t)jc.size());
   }
   // one blob: staged block first, then the team-only tables
   StageLayout L{};
@@ -375,14 +381,17 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   L.tab = place(sizeof(double) * 256);
   L.bytes = (uint32_t)off;
   const size_t off_csr_ptr = place(sizeof(int32_t) * (S + 1));
-  const size_t off_csr_rx = place(sizeof(int32_t) * csr_rx.size());
-  const size_t off_csr_nu = place(sizeof(double) * csr_nu.size());
+  std::vector<CsrTerm> csr(csr_rx.size());
+  for (size_t e = 0; e < csr.size(); ++e) {
+    csr[e].nu = csr_nu[e];
+    csr[e].rx = csr_rx[e];
+    csr[e].pad = 0;
+  }
+  const size_t off_csr = place(sizeof(CsrTerm) * csr.size());
   const size_t off_csr_cptr = place(sizeof(int32_t) * csr_cptr.size());
   const size_t off_jc_ptr = place(sizeof(int32_t) * jc_ptr.size());
-  const size_t off_jc_idx = place(sizeof(int32_t) * jc_idx.size());
-  const size_t off_jc_cp = place(sizeof(int32_t) * jc_cp.size());
-  const size_t off_con_coef = place(sizeof(double) * con_coef.size());
-  const size_t off_con_pidx = place(sizeof(int32_t) * con_pidx.size());
+  const size_t off_jc = place(sizeof(JcEntry) * jc.size());
+  const size_t off_jt = place(sizeof(JcTerm) * jt.size());
   const size_t off_err = place(sizeof(int32_t) * 4);
   const size_t total = off;
   std::vector<unsigned char> host(total, 0);
@@ -399,14 +408,11 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   put(L.revp, revp.data(), sizeof(double) * revp.size());
   put(L.tab, tab.data(), sizeof(double) * 256);
   put(off_csr_ptr, csr_ptr.data(), sizeof(int32_t) * (S + 1));
-  put(off_csr_rx, csr_rx.data(), sizeof(int32_t) * csr_rx.size());
-  put(off_csr_nu, csr_nu.data(), sizeof(double) * csr_nu.size());
+  put(off_csr, csr.data(), sizeof(CsrTerm) * csr.size());
   put(off_csr_cptr, csr_cptr.data(), sizeof(int32_t) * csr_cptr.size());
   put(off_jc_ptr, jc_ptr.data(), sizeof(int32_t) * jc_ptr.size());
-  put(off_jc_idx, jc_idx.data(), sizeof(int32_t) * jc_idx.size());
-  put(off_jc_cp, jc_cp.data(), sizeof(int32_t) * jc_cp.size());
-  put(off_con_coef, con_coef.data(), sizeof(double) * con_coef.size());
-  put(off_con_pidx, con_pidx.data(), sizeof(int32_t) * con_pidx.size());
+  put(off_jc, jc.data(), sizeof(JcEntry) * jc.size());
+  put(off_jt, jt.data(), sizeof(JcTerm) * jt.size());
 
   ck_mech* m = new ck_mech;
   HostMech& hm = m->hm;
@@ -449,17 +455,14 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   dm.eff_m1 = reinterpret_cast<const double*>(b + L.eff_m1);
   dm.tab = reinterpret_cast<const double*>(b + L.tab);
   dm.csr_ptr = reinterpret_cast<const int32_t*>(b + off_csr_ptr);
-  dm.csr_rx = reinterpret_cast<const int32_t*>(b + off_csr_rx);
-  dm.csr_nu = reinterpret_cast<const double*>(b + off_csr_nu);
+  dm.csr = reinterpret_cast<const CsrTerm*>(b + off_csr);
   dm.chunk = chunk;
   dm.n_chunks = n_chunks;
   dm.csr_cptr = reinterpret_cast<const int32_t*>(b + off_csr_cptr);
   dm.jc_ptr = reinterpret_cast<const int32_t*>(b + off_jc_ptr);
-  dm.jc_idx = reinterpret_cast<const int32_t*>(b + off_jc_idx);
-  dm.jc_cp = reinterpret_cast<const int32_t*>(b + off_jc_cp);
-  dm.con_coef = reinterpret_cast<const double*>(b + off_con_coef);
-  dm.con_pidx = reinterpret_cast<const int32_t*>(b + off_con_pidx);
-  hm.n_contrib = (int)con_coef.size();
+  dm.jc = reinterpret_cast<const JcEntry*>(b + off_jc);
+  dm.jt = reinterpret_cast<const JcTerm*>(b + off_jt);
+  hm.n_contrib = (int)jt.size();
   hm.csr_nnz = (int)csr_rx.size();
   hm.dev_err = reinterpret_cast<int32_t*>(b + off_err);
   // resolve the allocation-free entry point's static scratch on this device

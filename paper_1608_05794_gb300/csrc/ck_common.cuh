@@ -55,6 +55,22 @@ constexpr int JP = 7;
 constexpr int TH_STRIDE = 18;
 constexpr int TH_PER_SPECIES = 2 * TH_STRIDE;
 
+// Packed team-kernel table records (one 16-byte load each).
+struct __align__(16) CsrTerm {  // species -> reaction list: net coefficient and reaction
+  double nu;
+  int32_t rx, pad;
+};
+struct __align__(16) JcEntry {  // one species-block entry of the Jacobian assembly
+  int32_t idx;                  // flat shared-memory index of the entry
+  int32_t beg, end;             // its contribution terms
+  int32_t pad;
+};
+struct __align__(16) JcTerm {   // coef * P[pidx]
+  double coef;
+  int32_t pidx, pad;
+};
+static_assert(sizeof(CsrTerm) == 16 && sizeof(JcEntry) == 16 && sizeof(JcTerm) == 16, "packed records");
+
 // Device view of a loaded mechanism.  All pointers are device memory (one
 // allocation, 16-byte aligned sections).
 struct DevMech {
@@ -72,24 +88,20 @@ struct DevMech {
   const int16_t* eff_sp;  // [n_eff]
   const double* eff_m1;   // [n_eff] efficiency - 1
   const int32_t* csr_ptr; // [S+1] species -> (reaction, net nu) lists
-  const int32_t* csr_rx;  // [csr_nnz] reaction index
-  const double* csr_nu;   // [csr_nnz] net stoichiometric coefficient
+  const CsrTerm* csr;     // [csr_nnz]
   const double* tab;      // [256] 2^(j/256)
   const double* revp;     // [n_rev][3] explicit reverse: log2 A_r, beta_r, Ea_r / (R ln 2)
   // Team kernels walk the reactions in chunks of `chunk` (= CTA size).
   // csr_cptr[k (n_chunks + 1) + c] = first CSR entry of species k whose
   // reaction lies in chunk c or later.  Jacobian assembly, chunk c: the
-  // entries e in [jc_ptr[c], jc_ptr[c+1]) of the species block A (flat
-  // shared-memory index jc_idx[e]) add the sum over t in [jc_cp[e],
-  // jc_cp[e+1]) of con_coef[t] * P[con_pidx[t]] (P: the chunk's partials,
-  // JP per reaction).
+  // entries jc[e], e in [jc_ptr[c], jc_ptr[c+1]), of the species block A
+  // each add the sum over t in [jc[e].beg, jc[e].end) of jt[t].coef *
+  // P[jt[t].pidx] (P: the chunk's partials, JP per reaction).
   int chunk, n_chunks;
   const int32_t* csr_cptr;
   const int32_t* jc_ptr;
-  const int32_t* jc_idx;
-  const int32_t* jc_cp;
-  const double* con_coef;
-  const int32_t* con_pidx;
+  const JcEntry* jc;
+  const JcTerm* jt;
 };
 
 // ---------------------------------------------------------------- 2^x

@@ -119,6 +119,17 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
   x.Ctot = team_sum(c, b.red);
 }
 
+// A 96-byte reaction record in six 16-byte loads (the fields are then read
+// from registers).
+__device__ __forceinline__ RxnRec load_rxn(const RxnRec* src) {
+  RxnRec r;
+  const int4* s = reinterpret_cast<const int4*>(src);
+  int4* t = reinterpret_cast<int4*>(&r);
+#pragma unroll
+  for (int q = 0; q < 6; ++q) t[q] = __ldg(s + q);
+  return r;
+}
+
 // Rates of one reaction at the mixture state.  With want_jac also the
 // partial-derivative pieces used by the Jacobian (see team_jacobian).
 __device__ __forceinline__ void team_reaction(const DevMech& m, const RxnRec& r, const Mix& x,
@@ -249,11 +260,17 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
     // scratch (q, dqT, D, P are contiguous) holds every rate of progress at
     // once: one reaction pass and one gather, two barriers in all.  The
     // gather sums in the same order as the chunked form below.
-    for (int i = threadIdx.x; i < m.R; i += blockDim.x) team_reaction(m, m.rxn[i], x, b, tab, i, false);
+    for (int i = threadIdx.x; i < m.R; i += blockDim.x) {
+      const RxnRec r = load_rxn(m.rxn + i);
+      team_reaction(m, r, x, b, tab, i, false);
+    }
     team_sync();
     for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
       double w = b.wd[k];
-      for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) w = fma(m.csr_nu[e], b.q[m.csr_rx[e]], w);
+      for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) {
+        const CsrTerm t = m.csr[e];
+        w = fma(t.nu, b.q[t.rx], w);
+      }
       b.wd[k] = w;
     }
     team_sync();
@@ -261,12 +278,18 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
     for (int c = 0; c < NC; ++c) {
       const int base = c * CH;
       for (int li = threadIdx.x; li < CH; li += blockDim.x)
-        if (base + li < m.R) team_reaction(m, m.rxn[base + li], x, b, tab, li, false);
+        if (base + li < m.R) {
+          const RxnRec r = load_rxn(m.rxn + base + li);
+          team_reaction(m, r, x, b, tab, li, false);
+        }
       team_sync();
       for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
         const int* cp = m.csr_cptr + k * (NC + 1) + c;
         double w = b.wd[k];
-        for (int e = cp[0]; e < cp[1]; ++e) w = fma(m.csr_nu[e], b.q[m.csr_rx[e] - base], w);
+        for (int e = cp[0]; e < cp[1]; ++e) {
+          const CsrTerm t = m.csr[e];
+          w = fma(t.nu, b.q[t.rx - base], w);
+        }
         b.wd[k] = w;
       }
       team_sync();
@@ -320,19 +343,27 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   for (int c = 0; c < NC; ++c) {
     const int base = c * CH;
     for (int li = threadIdx.x; li < CH; li += blockDim.x)
-      if (base + li < m.R) team_reaction(m, m.rxn[base + li], x, b, tab, li, true);
+      if (base + li < m.R) {
+        const RxnRec r = load_rxn(m.rxn + base + li);
+        team_reaction(m, r, x, b, tab, li, true);
+      }
     team_sync();
     for (int e = m.jc_ptr[c] + threadIdx.x; e < m.jc_ptr[c + 1]; e += blockDim.x) {
-      double a = J[m.jc_idx[e]];
-      for (int t = m.jc_cp[e]; t < m.jc_cp[e + 1]; ++t) a = fma(m.con_coef[t], b.P[m.con_pidx[t]], a);
-      J[m.jc_idx[e]] = a;
+      const JcEntry h = m.jc[e];
+      double a = J[h.idx];
+      for (int t = h.beg; t < h.end; ++t) {
+        const JcTerm ct = m.jt[t];
+        a = fma(ct.coef, b.P[ct.pidx], a);
+      }
+      J[h.idx] = a;
     }
     for (int k = threadIdx.x; k < S; k += blockDim.x) {
       const int* cp = m.csr_cptr + k * (NC + 1) + c;
       double w = b.wd[k], aT = b.aT[k], E = b.E[k], u = b.u[k];
       for (int e = cp[0]; e < cp[1]; ++e) {
-        const int li = m.csr_rx[e] - base;
-        const double nu = m.csr_nu[e];
+        const CsrTerm ct = m.csr[e];
+        const int li = ct.rx - base;
+        const double nu = ct.nu;
         w = fma(nu, b.q[li], w);
         aT = fma(nu, b.dqT[li], aT);
         E = fma(nu, b.D[li], E);
