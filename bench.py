@@ -494,7 +494,8 @@ def run_ours(args):
                 "config": _config_dict(cfg), "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
                 "gpu_launches": 3 * args.steps, "clocks": clocks,
                 "rhs_evals_per_s": rhs_rate, "rhs_repeats": args.rhs_repeats, "breakdown": breakdown,
-                "fp64_probe": peaks, "parity_sample": parity_sample, "all_reactors_ok": st_ok}
+                "fp64_probe": peaks, "work_per_unit": work, "parity_sample": parity_sample,
+                "all_reactors_ok": st_ok}
         line.update(ext)
         print(json.dumps(line), flush=True)
     if world > 1:
@@ -982,6 +983,21 @@ def run_precision(args):
                       "dt": "each workload's", "results": res}), flush=True)
 
 
+def run_counts(args):
+    """The algorithmic work per unit of the three workloads' mechanisms
+    (ck_count_work): flops in the roofline's model, transcendentals, and the
+    FP64 instructions of the library's formulation."""
+    import torch
+    torch.cuda.set_device(0)
+    import paper_1608_05794_gb300.ck as ck
+    from synth.configs import CONFIGS, load_mechanism
+    out = {}
+    for name in ("small", "medium", "large"):
+        m = load_mechanism(CONFIGS[name]["mech"])
+        out[name] = dict(ck.count_work(ck.load_mechanism(m)), species=len(m["mw"]), reactions=len(m["rtype"]))
+    print(json.dumps({"mode": "counts", "work": out}), flush=True)
+
+
 def run_peak(args):
     """The FP64 roofline denominators alone: FMA throughput and the cost of
     the library's 2^x, with the SM clock sampled during the probe."""
@@ -1050,7 +1066,7 @@ def main():
     ap.add_argument("--workload", choices=["small", "medium", "large"], default=None,
                     help="workload of --profile-case (default: medium)")
     ap.add_argument("--precision", type=int, default=0, help="ROS4 precision form of --profile-case")
-    ap.add_argument("--mode", choices=["bench", "serve", "batch", "fdjac", "variants", "precision", "peak"],
+    ap.add_argument("--mode", choices=["bench", "serve", "batch", "fdjac", "variants", "precision", "peak", "counts"],
                     default="bench")
     ap.add_argument("--precision-reactors", type=int, default=32768, help="precision: medium reactors (large: half)")
     ap.add_argument("--variant-reactors", type=int, default=32768, help="variants: medium-workload reactors")
@@ -1080,6 +1096,8 @@ def main():
         run_batch(args)
     elif args.mode == "peak":
         run_peak(args)
+    elif args.mode == "counts":
+        run_counts(args)
     elif args.profile_case:
         run_profile_case(args)
     elif args.impl == "reference":
