@@ -312,14 +312,24 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
       csr_cptr[(size_t)k * (n_chunks + 1) + c] = (c == n_chunks) ? csr_ptr[k + 1] : e;
     }
   }
-  // Jacobian contributions, chunk by chunk: A[k][j] += nu_ki * P[i][slot] for
-  // every slot of reaction i holding species j (and nu_ki (eff_ij - 1) *
-  // P[i][6] for the third-body corrections), grouped by entry (k, j)
+  // Jacobian assembly, chunk by chunk, as one list of targets, each adding a
+  // fixed-order sum of coef * src[pidx] (src: the chunk's per-reaction
+  // arrays q, dq/dT, D and the partials P, contiguous in shared memory):
+  // - species-block entries A[k][j] += nu_ki * P[i][slot] for every slot of
+  //   reaction i holding species j (and nu_ki (eff_ij - 1) * P[i][6] for the
+  //   third-body corrections), target index (1 + k) n + 1 + j;
+  // - per species k the four sums over its reactions in the chunk, wdot_k
+  //   (nu q), a_k (nu dq/dT), E_k (nu D) and u_k (nu P[i][6]), target index
+  //   n^2 + a S + k for a = 0..3, terms in the CSR order.
+  // Longest lists first, so that lanes running the same iteration do similar
+  // amounts of work.
   std::vector<int32_t> jc_ptr(1, 0);
   std::vector<JcEntry> jc;
   std::vector<JcTerm> jt;
+  int n_jterms = 0;
+  const int NN = (S + 1) * (S + 1);
   for (int c = 0; c < n_chunks; ++c) {
-    std::vector<std::vector<std::pair<double, int32_t>>> ent((size_t)S * S);
+    std::vector<std::vector<std::pair<double, int32_t>>> ent((size_t)S * S + 4 * (size_t)S);
     for (int k = 0; k < S; ++k) {
       for (int e = csr_cptr[(size_t)k * (n_chunks + 1) + c]; e < csr_cptr[(size_t)k * (n_chunks + 1) + c + 1];
            ++e) {
@@ -327,29 +337,38 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
         const int li = i - c * chunk;
         const double nu = csr_nu[e];
         const RxnRec& r = rx[i];
+        const int32_t pbase = 3 * chunk + li * JP;
         // coefficients carry W_k / W_j, the factor of the species block
         // dY_k/dY_j (so the assembly needs no per-entry rescaling)
         auto wr = [&](int j) { return (double)((long double)W[k] / (long double)W[j]); };
         for (int s2 = 0; s2 < r.nreac; ++s2)
-          ent[(size_t)k * S + r.sp[s2]].push_back({nu * wr(r.sp[s2]), li * JP + s2});
+          ent[(size_t)k * S + r.sp[s2]].push_back({nu * wr(r.sp[s2]), pbase + s2});
         if (r.rev)
           for (int s2 = 0; s2 < r.nprod; ++s2)
-            ent[(size_t)k * S + r.sp[3 + s2]].push_back({nu * wr(r.sp[3 + s2]), li * JP + 3 + s2});
+            ent[(size_t)k * S + r.sp[3 + s2]].push_back({nu * wr(r.sp[3 + s2]), pbase + 3 + s2});
         for (int q = r.eff_beg; q < r.eff_beg + r.eff_cnt; ++q)
-          ent[(size_t)k * S + eff_sp[q]].push_back({nu * eff_m1[q] * wr(eff_sp[q]), li * JP + 6});
+          ent[(size_t)k * S + eff_sp[q]].push_back({nu * eff_m1[q] * wr(eff_sp[q]), pbase + 6});
+        const size_t sb = (size_t)S * S;
+        ent[sb + 0 * S + k].push_back({nu, li});
+        ent[sb + 1 * S + k].push_back({nu, chunk + li});
+        ent[sb + 2 * S + k].push_back({nu, 2 * chunk + li});
+        ent[sb + 3 * S + k].push_back({nu, pbase + 6});
       }
     }
     std::vector<int> order_e;
-    for (int e = 0; e < S * S; ++e)
-      if (!ent[e].empty()) order_e.push_back(e);
-    // longest lists first, so that lanes running the same iteration do
-    // similar amounts of work
+    for (size_t e = 0; e < ent.size(); ++e)
+      if (!ent[e].empty()) order_e.push_back((int)e);
     std::stable_sort(order_e.begin(), order_e.end(),
                      [&](int a, int b) { return ent[a].size() > ent[b].size(); });
     for (int e : order_e) {
-      const int k = e / S, j = e % S;
       JcEntry h{};
-      h.idx = (1 + k) * (S + 1) + 1 + j;
+      if (e < S * S) {
+        const int k = e / S, j = e % S;
+        h.idx = (1 + k) * (S + 1) + 1 + j;
+        n_jterms += (int)ent[e].size();
+      } else {
+        h.idx = NN + (e - S * S);
+      }
       h.beg = (int32_t)jt.size();
       for (auto& cc : ent[e]) {
         JcTerm t{};
@@ -462,7 +481,7 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   dm.jc_ptr = reinterpret_cast<const int32_t*>(b + off_jc_ptr);
   dm.jc = reinterpret_cast<const JcEntry*>(b + off_jc);
   dm.jt = reinterpret_cast<const JcTerm*>(b + off_jt);
-  hm.n_contrib = (int)jt.size();
+  hm.n_contrib = n_jterms;
   hm.csr_nnz = (int)csr_rx.size();
   hm.dev_err = reinterpret_cast<int32_t*>(b + off_err);
   // resolve the allocation-free entry point's static scratch on this device

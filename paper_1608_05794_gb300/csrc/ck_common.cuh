@@ -94,9 +94,11 @@ struct DevMech {
   // Team kernels walk the reactions in chunks of `chunk` (= CTA size).
   // csr_cptr[k (n_chunks + 1) + c] = first CSR entry of species k whose
   // reaction lies in chunk c or later.  Jacobian assembly, chunk c: the
-  // entries jc[e], e in [jc_ptr[c], jc_ptr[c+1]), of the species block A
-  // each add the sum over t in [jc[e].beg, jc[e].end) of jt[t].coef *
-  // P[jt[t].pidx] (P: the chunk's partials, JP per reaction).
+  // targets jc[e], e in [jc_ptr[c], jc_ptr[c+1]) (flat index idx: the
+  // species-block entry J[idx] below n^2, else the per-species sums wd, aT,
+  // E, u at idx - n^2), each add the sum over t in [jc[e].beg, jc[e].end)
+  // of jt[t].coef * src[jt[t].pidx] (src: the chunk's q, dq/dT, D and
+  // partials P, JP per reaction, contiguous).
   int chunk, n_chunks;
   const int32_t* csr_cptr;
   const int32_t* jc_ptr;
@@ -113,27 +115,56 @@ struct DevMech {
 // exact (x - round_{1/256}(x) is representable), so the result is within
 // about one ulp.  |x| > 1000 (and NaN) falls back to the library exp2, out of
 // line so that the rarely taken branch adds no instructions to the inlined
-// fast path.
+// fast path.  The range test compares the bits of |x| as an integer (they
+// order like |x|, NaN above +inf), which keeps it off the FP64 pipe.
 static __device__ __noinline__ double ck_exp2_wide(double x) { return exp2(x); }
 
-__device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ tab) {
-  if (!(fabs(x) <= 1000.0)) return ck_exp2_wide(x);
-  const double SHIFT = 26388279066624.0;  // 1.5 * 2^44: ulp 2^-8
-  double t = x + SHIFT;
-  double kx = t - SHIFT;
-  double r = x - kx;
-  int i = (int)__double2loint(t);        // round(x * 256), low bits of t
-  int j = i & 255;
-  int e = i >> 8;                        // floor division by 256
+__device__ __forceinline__ bool ck_exp2_in_range(double x) {
+  const unsigned long long ax = (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+  return ax <= 0x408F400000000000ULL;  // the bits of 1000.0
+}
+
+// 2^r - 1 for |r| <= 1/512 (Taylor, degree 4 in r ln 2), and the step that
+// assembles 2^(e + j/256 + r) from it.
+__device__ __forceinline__ double ck_exp2_poly(double r) {
   const double c1 = 0.69314718055994530942;
   const double c2 = 0.24022650695910071233;   // ln2^2/2
   const double c3 = 0.055504108664821579953;  // ln2^3/6
   const double c4 = 0.0096181291076284771620; // ln2^4/24
-  double q = fma(fma(fma(c4, r, c3), r, c2), r, c1) * r;
-  double tj = tab[j];
-  double res = fma(tj, q, tj);
-  long long b = __double_as_longlong(res) + ((long long)e << 52);
-  return __longlong_as_double(b);
+  return fma(fma(fma(c4, r, c3), r, c2), r, c1) * r;
+}
+__device__ __forceinline__ double ck_exp2_assemble(int i, double q, const double* __restrict__ tab) {
+  const int j = i & 255;
+  const int e = i >> 8;  // floor division by 256
+  const double tj = tab[j];
+  const double res = fma(tj, q, tj);
+  return __longlong_as_double(__double_as_longlong(res) + ((long long)e << 52));
+}
+
+__device__ __forceinline__ double ck_exp2(double x, const double* __restrict__ tab) {
+  if (!ck_exp2_in_range(x)) return ck_exp2_wide(x);
+  const double SHIFT = 26388279066624.0;  // 1.5 * 2^44: ulp 2^-8
+  const double t = x + SHIFT;
+  const double r = x - (t - SHIFT);
+  const int i = (int)__double2loint(t);  // round(x * 256), low bits of t
+  return ck_exp2_assemble(i, ck_exp2_poly(r), tab);
+}
+
+// 2^x and 2^-x from one reduction.  Rounding x to a multiple of 1/256 is
+// symmetric (ties to even), so -x reduces to -i and -r exactly, and both
+// results are bitwise those of ck_exp2(x) and ck_exp2(-x).
+__device__ __forceinline__ void ck_exp2_pm(double x, const double* __restrict__ tab, double& ep, double& em) {
+  if (!ck_exp2_in_range(x)) {
+    ep = ck_exp2_wide(x);
+    em = ck_exp2_wide(-x);
+    return;
+  }
+  const double SHIFT = 26388279066624.0;
+  const double t = x + SHIFT;
+  const double r = x - (t - SHIFT);
+  const int i = (int)__double2loint(t);
+  ep = ck_exp2_assemble(i, ck_exp2_poly(r), tab);
+  em = ck_exp2_assemble(-i, ck_exp2_poly(-r), tab);
 }
 
 // 1 / x rounded to nearest: the value IEEE division 1 / x returns, without

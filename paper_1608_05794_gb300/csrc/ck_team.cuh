@@ -104,8 +104,7 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
     g = fma(a[15], x.T3, g);
     g = fma(a[16], x.T4, g);
     g = fma(a[17], x.invT, g);
-    b.Gp[k] = ck_exp2(g, tab);
-    b.Gm[k] = ck_exp2(-g, tab);
+    ck_exp2_pm(g, tab, b.Gp[k], b.Gm[k]);
     b.cpR[k] = fma(a[4], x.T4, fma(a[3], x.T3, fma(a[2], x.T2, fma(a[1], x.T, a[0]))));
     b.hRT[k] = fma(a[10], x.invT, fma(a[9], x.T4, fma(a[8], x.T3, fma(a[7], x.T2, fma(a[6], x.T, a[5])))));
     if (want_dcp)
@@ -333,10 +332,10 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   team_species(m, p, y, b, x, true, tab);
   // species block A starts at zero (the whole matrix is cleared: the
   // temperature row and column are written whole further down); chunk by
-  // chunk, every entry touched by the chunk adds its fixed-order sum of
-  // contributions (one thread per entry, no conflicts), and every species
-  // adds its terms of wdot, d wdot/dT, E = sum nu D and the dense
-  // third-body part u
+  // chunk, every entry touched by the chunk and every species sum (wdot,
+  // d wdot/dT, E = sum nu D and the dense third-body part u) adds its
+  // fixed-order sum of contributions, one thread per target, the targets in
+  // one list sorted by length so that a warp's lanes do similar work
   for (int e = threadIdx.x; e < n * n; e += blockDim.x) J[e] = 0.0;
   team_sync();
   const int NC = m.n_chunks, CH = m.chunk;
@@ -348,31 +347,18 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
         team_reaction(m, r, x, b, tab, li, true);
       }
     team_sync();
+    // every target of the chunk (species-block entries and the per-species
+    // sums wdot, a, E, u, whose arrays wd, aT, E, u are contiguous) adds its
+    // fixed-order sum of terms; one thread per target, no conflicts
     for (int e = m.jc_ptr[c] + threadIdx.x; e < m.jc_ptr[c + 1]; e += blockDim.x) {
       const JcEntry h = m.jc[e];
-      double a = J[h.idx];
+      double* tgt = h.idx < n * n ? J + h.idx : b.wd + (h.idx - n * n);
+      double a = *tgt;
       for (int t = h.beg; t < h.end; ++t) {
         const JcTerm ct = m.jt[t];
-        a = fma(ct.coef, b.P[ct.pidx], a);
+        a = fma(ct.coef, b.q[ct.pidx], a);
       }
-      J[h.idx] = a;
-    }
-    for (int k = threadIdx.x; k < S; k += blockDim.x) {
-      const int* cp = m.csr_cptr + k * (NC + 1) + c;
-      double w = b.wd[k], aT = b.aT[k], E = b.E[k], u = b.u[k];
-      for (int e = cp[0]; e < cp[1]; ++e) {
-        const CsrTerm ct = m.csr[e];
-        const int li = ct.rx - base;
-        const double nu = ct.nu;
-        w = fma(nu, b.q[li], w);
-        aT = fma(nu, b.dqT[li], aT);
-        E = fma(nu, b.D[li], E);
-        u = fma(nu, b.P[(size_t)li * JP + 6], u);
-      }
-      b.wd[k] = w;
-      b.aT[k] = aT;
-      b.E[k] = E;
-      b.u[k] = u;
+      *tgt = a;
     }
     team_sync();
   }

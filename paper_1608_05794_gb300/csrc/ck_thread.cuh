@@ -58,8 +58,7 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
     g = fma(a[15], T3, g);
     g = fma(a[16], T4, g);
     g = fma(a[17], invT, g);
-    G[k] = ck_exp2(g, m.tab);
-    G[S + k] = ck_exp2(-g, m.tab);
+    ck_exp2_pm(g, m.tab, G[k], G[S + k]);
     wd[k] = 0.0;
   }
   const double* Gm = G + S;
