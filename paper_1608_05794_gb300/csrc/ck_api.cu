@@ -381,6 +381,17 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
     }
     jc_ptr.push_back((int32_t)jc.size());
   }
+  // species ordered by the length of their CSR rows (longest first), so
+  // that the lanes of one warp gather similar counts in the one-pass RHS
+  std::vector<int16_t> rsp(S);
+  {
+    std::vector<int> ks(S);
+    for (int k = 0; k < S; ++k) ks[k] = k;
+    std::stable_sort(ks.begin(), ks.end(), [&](int a, int b) {
+      return csr_ptr[a + 1] - csr_ptr[a] > csr_ptr[b + 1] - csr_ptr[b];
+    });
+    for (int k = 0; k < S; ++k) rsp[k] = (int16_t)ks[k];
+  }
   // one blob: staged block first, then the team-only tables
   StageLayout L{};
   size_t off = 0;
@@ -411,6 +422,7 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   const size_t off_jc_ptr = place(sizeof(int32_t) * jc_ptr.size());
   const size_t off_jc = place(sizeof(JcEntry) * jc.size());
   const size_t off_jt = place(sizeof(JcTerm) * jt.size());
+  const size_t off_rsp = place(sizeof(int16_t) * rsp.size());
   const size_t off_err = place(sizeof(int32_t) * 4);
   const size_t total = off;
   std::vector<unsigned char> host(total, 0);
@@ -432,6 +444,7 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   put(off_jc_ptr, jc_ptr.data(), sizeof(int32_t) * jc_ptr.size());
   put(off_jc, jc.data(), sizeof(JcEntry) * jc.size());
   put(off_jt, jt.data(), sizeof(JcTerm) * jt.size());
+  put(off_rsp, rsp.data(), sizeof(int16_t) * rsp.size());
 
   ck_mech* m = new ck_mech;
   HostMech& hm = m->hm;
@@ -481,6 +494,7 @@ int ck_load_mechanism(const ck_mech_desc* d, ck_mech** out) {
   dm.jc_ptr = reinterpret_cast<const int32_t*>(b + off_jc_ptr);
   dm.jc = reinterpret_cast<const JcEntry*>(b + off_jc);
   dm.jt = reinterpret_cast<const JcTerm*>(b + off_jt);
+  dm.rsp = reinterpret_cast<const int16_t*>(b + off_rsp);
   hm.n_contrib = n_jterms;
   hm.csr_nnz = (int)csr_rx.size();
   hm.dev_err = reinterpret_cast<int32_t*>(b + off_err);

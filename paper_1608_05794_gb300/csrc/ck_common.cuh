@@ -104,6 +104,7 @@ struct DevMech {
   const int32_t* jc_ptr;
   const JcEntry* jc;
   const JcTerm* jt;
+  const int16_t* rsp;     // [S] species order of the one-pass RHS gather, longest row first
 };
 
 // ---------------------------------------------------------------- 2^x

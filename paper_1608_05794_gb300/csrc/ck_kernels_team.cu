@@ -211,18 +211,19 @@ __global__ void __launch_bounds__(64) k_rkf45_team(const __grid_constant__ DevMe
           continue;
         }
         last_nf = false;
+        const double pe = (e == 0.0) ? 0.0 : team_pow(e, -0.2, b.red);
         if (e < 1.0) {
           for (int i = tid; i < n; i += P) yv[i] = yt[i];
           team_sync();
           t = clamped ? tf : t + hh;
           ++acc;
-          double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(e, -0.2)));
+          double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pe));
           if (last_rej) fac = fmin(1.0, fac);
           h = hh * fac;
           last_rej = false;
         } else {
           ++rej;
-          h = hh * fmax(FAC_MIN, SAFETY * pow(e, -0.2));
+          h = hh * fmax(FAC_MIN, SAFETY * pe);
           last_rej = true;
         }
       }

@@ -246,19 +246,20 @@ __global__ void __launch_bounds__(G * G, G == 8 ? 6 : 1) k_ros4(const __grid_con
           continue;
         }
         last_nf = false;
+        const double pe = (e == 0.0) ? 0.0 : team_pow(e, -0.25, b.red);
         if (e < 1.0) {
           for (int i = tid; i < n; i += P) yv[i] = Yt[i];
           team_sync();
           t = clamped ? tf : t + hh;
           ++acc;
           have_j = have_f = false;
-          double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pow(e, -0.25)));
+          double fac = (e == 0.0) ? FAC_MAX : fmin(FAC_MAX, fmax(FAC_MIN, SAFETY * pe));
           if (last_rej) fac = fmin(1.0, fac);
           h = hh * fac;
           last_rej = false;
         } else {
           ++rej;
-          h = hh * fmax(FAC_MIN, SAFETY * pow(e, -0.25));
+          h = hh * fmax(FAC_MIN, SAFETY * pe);
           last_rej = true;
         }
       }

@@ -50,7 +50,7 @@ struct TeamBufs {
 
 // Mixture quantities shared by the RHS and the Jacobian.
 struct Mix {
-  double T, invT, lnT, log2T, T2, T3, T4, rho, Wbar, Ctot;
+  double T, invT, lnT, log2T, T2, T3, T4, rho, invrho, Wbar, Ctot;
   double dcpm;  // this thread's part of sum_k Y_k/W_k d(cp_k/R)/dT (Jacobian only)
 };
 
@@ -90,8 +90,27 @@ __device__ __forceinline__ void team_species(const DevMech& m, double p, const d
     x.T3 = tf[4];
     x.T4 = tf[5];
   }
-  x.Wbar = rcp_rn(sumYW);
-  x.rho = m.cv ? p : p / (R_GAS * x.T * sumYW);  // constant volume: p is the density
+  // the mean molar mass, rho and 1 / rho likewise by the first warp,
+  // through red[32..34]
+  double* sc = b.red + 32;
+  if (threadIdx.x < 32) {
+    x.Wbar = rcp_rn(sumYW);
+    x.rho = m.cv ? p : p / (R_GAS * x.T * sumYW);  // constant volume: p is the density
+    x.invrho = rcp_rn(x.rho);
+    if (threadIdx.x == 0) {
+      sc[0] = x.Wbar;
+      sc[1] = x.rho;
+      sc[2] = x.invrho;
+    }
+  }
+  if (blockDim.x > 32) {
+    __syncthreads();
+    if (threadIdx.x >= 32) {
+      x.Wbar = sc[0];
+      x.rho = sc[1];
+      x.invrho = sc[2];
+    }
+  }
   double c = 0.0, dcpm = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
     const double xk = x.rho * (y[1 + k] * m.invW[k]);
@@ -264,7 +283,8 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
       team_reaction(m, r, x, b, tab, i, false);
     }
     team_sync();
-    for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
+    for (int kk = threadIdx.x; kk < m.S; kk += blockDim.x) {
+      const int k = m.rsp[kk];
       double w = b.wd[k];
       for (int e = m.csr_ptr[k]; e < m.csr_ptr[k + 1]; ++e) {
         const CsrTerm t = m.csr[e];
@@ -294,7 +314,7 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
       team_sync();
     }
   }
-  const double invrho = rcp_rn(x.rho);
+  const double invrho = x.invrho;
   const double cvf = m.cv ? 1.0 : 0.0;  // constant volume: U/RT = H/RT - 1, cv/R = cp/R - 1
   double cpm = 0.0, hw = 0.0;
   for (int k = threadIdx.x; k < m.S; k += blockDim.x) {
@@ -367,7 +387,7 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   // d rho/dY (cpf) drops out, and U/RT = H/RT - 1, cv/R = cp/R - 1 take the
   // places of H/RT and cp/R (cvf).  The contributions were pre-scaled by
   // W_k/W_j, so J holds A'_kj = W_k A_kj / W_j here.
-  const double invrho = rcp_rn(x.rho);
+  const double invrho = x.invrho;
   const double cvf = m.cv ? 1.0 : 0.0, cpf = 1.0 - cvf;
   double cpm = 0.0, hw = 0.0, he = 0.0, dcpm = x.dcpm, cw = 0.0, ha = 0.0, eu = 0.0;
   for (int k = threadIdx.x; k < S; k += blockDim.x) {
@@ -392,7 +412,18 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   cw = team_sum(cw, b.red);
   ha = team_sum(ha, b.red);
   eu = team_sum(eu, b.red);
-  const double Tdot = -x.T * hw / (x.rho * cpm);
+  // Tdot and 1 / cpm by the first warp, handed over through red[35..36]
+  // across the barrier below
+  double Tdot = 0.0, inv_cpm = 0.0;
+  double* sc = b.red + 32;
+  if (threadIdx.x < 32) {
+    Tdot = -x.T * hw / (x.rho * cpm);
+    inv_cpm = rcp_rn(cpm);
+    if (threadIdx.x == 0) {
+      sc[3] = Tdot;
+      sc[4] = inv_cpm;
+    }
+  }
   // cs_j = sum_k e_k (A_kj + u_k) = W_j sum_k (e_k / W_k) A'_kj + sum_k e_k u_k
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
     double s = 0.0;
@@ -400,6 +431,10 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
     b.cs[j] = fma(m.W[j], s, eu);
   }
   team_sync();
+  if (threadIdx.x >= 32) {
+    Tdot = sc[3];
+    inv_cpm = sc[4];
+  }
   // species block (J_kj = A'_kj + dense_k / W_j) and temperature column
   // entries e = k S + j of the species block, (k, j) advanced without
   // dividing by the runtime S
@@ -419,7 +454,6 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
   }
   for (int k = threadIdx.x; k < S; k += blockDim.x)
     J[(size_t)(1 + k) * n] = m.W[k] * invrho * fma(cpf * b.wd[k], x.invT, b.aT[k]);
-  const double inv_cpm = rcp_rn(cpm);
   const double inv_rc = invrho * inv_cpm;
   for (int j = threadIdx.x; j < S; j += blockDim.x) {
     const double t1 = x.T * (x.rho * b.cs[j] - cpf * x.Wbar * he) * inv_rc;
@@ -617,6 +651,11 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
   F u[T];
 #pragma unroll
   for (int c = KQ; c < T; ++c) u[c] = c < tn ? ub[tc + G * c] : F(0);
+  // slot column KQ needs work only in warps holding a column >= k (the G
+  // lanes of a column are consecutive, so the warp's largest tc is its last
+  // lane's): a warp-uniform test that lets the other warps skip it.  The
+  // FP32 factorization of the precision form measured faster without it.
+  const bool wcol = sizeof(F) < 8 || ((tid | 31) / G) >= kt;
 #pragma unroll
   for (int r = KQ; r < T; ++r) {
     if (r >= tn) break;
@@ -627,8 +666,10 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
       if (c >= tn) break;
       a[r][c] = fma(-li, u[c], a[r][c]);
     }
-    if (tc > kt) a[r][KQ] = fma(-li, u[KQ], a[r][KQ]);
-    else if (tc == kt && live) a[r][KQ] = li;
+    if (wcol) {
+      if (tc > kt) a[r][KQ] = fma(-li, u[KQ], a[r][KQ]);
+      else if (tc == kt && live) a[r][KQ] = li;
+    }
   }
   return true;
 }

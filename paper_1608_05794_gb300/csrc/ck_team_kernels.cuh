@@ -76,6 +76,17 @@ static __device__ __noinline__ void team_jacobian_fd(const DevMech& d, const dou
   }
 }
 
+// x^q, the step-size controller's power, by the first warp alone and handed
+// to the others through red[37]: pow is long, and every warp that runs it
+// pays all of its FP64 instructions.  x is the same in every thread; every
+// thread must call it.
+static __device__ __forceinline__ double team_pow(double x, double q, double* red) {
+  if (blockDim.x == 32) return pow(x, q);
+  if (threadIdx.x == 0) red[37] = pow(x, q);
+  __syncthreads();
+  return red[37];
+}
+
 // ------------------------------------------------------------------ ROS4
 // Weighted RMS norm over the team (reading shared with the oracle:
 // sqrt(mean (e_i / (atol + rtol max(|y_i|, |ynew_i|)))^2)).
