@@ -29,6 +29,28 @@ __device__ __forceinline__ double team_sum(double v, double* red) {
   return s;
 }
 
+// K block-wide sums at once (each in the order of team_sum, so the values
+// are those of K calls), with one pair of barriers.  K <= 4, blockDim <= 256.
+template <int K>
+__device__ __forceinline__ void team_sum_n(double (&v)[K], double* red) {
+#pragma unroll
+  for (int q = 0; q < K; ++q) v[q] = warp_allsum(v[q]);
+  const int nw = blockDim.x >> 5;
+  if (nw == 1) return;
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) {
+#pragma unroll
+    for (int q = 0; q < K; ++q) red[8 * q + (threadIdx.x >> 5)] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < K; ++q) {
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += red[8 * q + i];
+    v[q] = s;
+  }
+}
+
 __device__ __forceinline__ void team_sync() {
   if (blockDim.x == 32) __syncwarp();
   else __syncthreads();
@@ -323,8 +345,10 @@ static __device__ __noinline__ void team_rhs(const DevMech& m, const double* tab
     hw = fma(b.hRT[k] - cvf, w, hw);
     f[1 + k] = w * (m.W[k] * invrho);
   }
-  cpm = team_sum(cpm, b.red);
-  hw = team_sum(hw, b.red);
+  double sums[2] = {cpm, hw};
+  team_sum_n(sums, b.red);
+  cpm = sums[0];
+  hw = sums[1];
   if (threadIdx.x == 0) f[0] = -x.T * hw / (x.rho * cpm);
   team_sync();
 }
@@ -405,13 +429,16 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
     b.hRT[k] = e * m.invW[k];
     b.u[k] = m.W[k] * fma(cpf * x.Wbar * invrho, b.wd[k] - b.E[k], b.u[k]);
   }
-  cpm = team_sum(cpm, b.red);
-  dcpm = team_sum(dcpm, b.red);
-  hw = team_sum(hw, b.red);
-  he = team_sum(he, b.red);
-  cw = team_sum(cw, b.red);
-  ha = team_sum(ha, b.red);
-  eu = team_sum(eu, b.red);
+  double s4[4] = {cpm, dcpm, hw, he}, s3[3] = {cw, ha, eu};
+  team_sum_n(s4, b.red);
+  team_sum_n(s3, b.red);
+  cpm = s4[0];
+  dcpm = s4[1];
+  hw = s4[2];
+  he = s4[3];
+  cw = s3[0];
+  ha = s3[1];
+  eu = s3[2];
   // Tdot and 1 / cpm by the first warp, handed over through red[35..36]
   // across the barrier below
   double Tdot = 0.0, inv_cpm = 0.0;
@@ -545,6 +572,80 @@ __device__ __forceinline__ void lu_slot_row_in(F (&a)[T][T], int ps, int tn, con
   }
 }
 
+// Pivot search of step k = KQ G + kt in its branch-free form, run by every
+// lane of the warp that holds column k: each group of G lanes searches its
+// own column, so the warp stays converged, and the group of column k alone
+// stores the multipliers (column k below the diagonal, as it stands after
+// the exchange of rows k and p, times 1 / pivot, each lane scaling its own
+// rows) in lb.  Returns the pivot row, or -1 when the pivot is zero or not
+// finite; ip receives 1 / pivot.  The results are bitwise those of the
+// owner-group form in lu_step.
+template <int G, int T, int KQ, bool FULL, class F>
+__device__ __forceinline__ int lu_pivot(const F (&a)[T][T], int n, int kt, F* scratch, F& ip) {
+  constexpr int GT = G * T;
+  const int tid = threadIdx.x, tr = tid % G, tc = tid / G;
+  const int k = KQ * G + kt;
+  const int tn = FULL ? T : (n + G - 1) / G;
+  F* lb = scratch + (k & 1) * GT;
+  const unsigned long long INFB = inf_key(F(0));
+  unsigned long long best = 0;
+  F bv = F(0);
+  int bi = n;
+#pragma unroll
+  for (int r = KQ; r < T; ++r) {
+    if (r >= tn) break;
+    const int i = tr + G * r;
+    const bool ok = (r > KQ || tr >= kt) && i < n;
+    const unsigned long long key = abs_key(a[r][KQ]);
+    const bool take = ok && (bi == n || key > best);
+    best = take ? key : best;
+    bv = take ? a[r][KQ] : bv;
+    bi = take ? i : bi;
+  }
+#pragma unroll
+  for (int off = 1; off < G; off <<= 1) {
+    const unsigned long long ok_ = __shfl_xor_sync(0xffffffffu, best, off, G);
+    const F ov = __shfl_xor_sync(0xffffffffu, bv, off, G);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, off, G);
+    const bool take = oi < n && (bi == n || ok_ > best || (ok_ == best && oi < bi));
+    best = take ? ok_ : best;
+    bv = take ? ov : bv;
+    bi = take ? oi : bi;
+  }
+  const int p = bi;
+  const bool sing = p >= n || best == 0 || best >= INFB;
+  const F akk = __shfl_sync(0xffffffffu, a[KQ][KQ], kt, G);
+  ip = rcp_rn(sing ? F(1) : bv);
+  if (tc == kt && !sing) {
+#pragma unroll
+    for (int r = KQ; r < T; ++r) {
+      if (r >= tn) break;
+      const int i = tr + G * r;
+      if (i > k && i < n) lb[i] = ((i == p) ? akk : a[r][KQ]) * ip;
+    }
+  }
+  return sing ? -1 : p;
+}
+
+// The pivot of step k, published by lane tr = 0 of column k's group.
+template <int G, bool PRE, class F>
+__device__ __forceinline__ void lu_publish(int k, int p, F ip, int* piv, F* invd, int* sp) {
+  const int tid = threadIdx.x;
+  if (tid / G == k % G && tid % G == 0) {
+    *sp = p;
+    if (p >= 0) {
+      invd[k] = ip;
+      if (PRE) {
+        const int t = piv[k];
+        piv[k] = piv[p];
+        piv[p] = t;
+      } else {
+        piv[k] = p;
+      }
+    }
+  }
+}
+
 // One pivot step at compile-time slot kq (see lu_reg).  Returns false when
 // the pivot is zero or not finite.
 template <int G, int T, int KQ, bool PRE, bool FULL, class F>
@@ -559,9 +660,18 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
   F* xb = scratch + 3 * GT;
   int* sp = reinterpret_cast<int*>(scratch + 4 * GT);
   const unsigned long long INFB = inf_key(F(0));
-  // 1. pivot search, reciprocal and multipliers: the warp holding column k
+  // 1. pivot search, reciprocal and multipliers: the warp holding column k.
+  // The branch-free form measured faster everywhere but in the full-tile
+  // FP64 factorization of the 8 x 8 team, which keeps the owner-group form.
+  constexpr bool BF = !(G == 8 && FULL && sizeof(F) == 8);
   const int owner_warp = (kt * G) >> 5;
-  if ((tid >> 5) == owner_warp) {
+  if constexpr (BF) {
+    if ((tid >> 5) == owner_warp) {
+      F ip;
+      const int p0 = lu_pivot<G, T, KQ, FULL>(a, n, kt, scratch, ip);
+      lu_publish<G, PRE>(k, p0, ip, piv, invd, sp);
+    }
+  } else if ((tid >> 5) == owner_warp) {
     const int base = (kt * G) & 31;  // first lane of the owner group
     bool sing = false;
     F ip = F(0);
@@ -713,7 +823,11 @@ __device__ int lu_reg(F* A, int n, int* piv, F* invd, F* scratch) {
 #pragma unroll
     for (int c = 0; c < T; ++c) {
       const int j = tc + G * c;
-      if (i < n && j < n) A[i * n + j] = (PRE && j > i) ? a[r][c] * di : a[r][c];
+      // slot (r, c) lies wholly above the diagonal when c > r and wholly
+      // below it when c < r (tr, tc < G), so only c == r needs the test
+      F v = a[r][c];
+      if (PRE && (c > r || (c == r && tc > tr))) v = a[r][c] * di;
+      if (i < n && j < n) A[i * n + j] = v;
     }
   }
   __syncthreads();
