@@ -1,8 +1,9 @@
 // Thread-per-reactor kernels: the right-hand side (Sec. 5.1 benchmark: many
 // independent RHS evaluations) and the RKF45 integrator (Sec. 2, App. B,
-// Algorithm 1 per lane).  The mechanism tables are staged once per CTA
-// into shared memory with a bulk TMA copy (cp.async.bulk + mbarrier); every
-// lane then reads the same reaction record at the same time (broadcast).
+// Algorithm 1 per lane).  Every lane reads the same reaction record at the
+// same time (broadcast).  Where that costs no residency (stage_pays) the
+// mechanism tables are staged once per CTA into shared memory with a bulk
+// TMA copy (cp.async.bulk + mbarrier); otherwise they are read through L1.
 #include <cuda_runtime.h>
 
 #include "ck_internal.h"
@@ -307,6 +308,30 @@ static bool stage_fits(const HostMech& hm, size_t* smem) {
   return *smem <= 200 * 1024;
 }
 
+// Stage the tables in shared memory (one bulk copy a CTA) only when the
+// copy costs the grid no resident blocks.  Every lane reads the same record
+// at the same time, so L1 serves the tables nearly as well; on GB300 the
+// staged copy of the 53- and 111-species mechanisms cut the residency, and
+// reading them through L1 instead made the RHS 15 and 37 % faster and the
+// thread-per-reactor RKF45 43 and 38 %.  The 10-species tables (3 KB) stay
+// staged.  Returns the dynamic shared memory to launch with.
+template <class K>
+static int stage_pays(const HostMech& hm, K kernel, int threads, size_t* smem) {
+  if (!stage_fits(hm, smem)) {
+    *smem = 0;
+    return 0;
+  }
+  if (*smem > 48 * 1024) cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)*smem);
+  int with = 0, without = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&with, kernel, threads, *smem);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&without, kernel, threads, 0);
+  if (with < without) {
+    *smem = 0;
+    return 0;
+  }
+  return 1;
+}
+
 template <class K>
 static int blocks_for(K kernel, int threads, size_t smem) {
   int per_sm = 0;
@@ -318,15 +343,10 @@ static int blocks_for(K kernel, int threads, size_t smem) {
 template <int MAXS>
 static cudaError_t rhs_impl(const HostMech& hm, int64_t n, const double* p, const double* y,
                             double* f, cudaStream_t st) {
-  // The tables are read through L1 rather than staged in shared memory:
-  // every lane reads the same record at the same time, and without the
-  // staging copy's shared memory the grid holds more resident blocks (one
-  // wave for 131072 reactors of the medium mechanism, 15 % more evaluations
-  // a second there and 37 % on the large one, measured on GB300).
-  const size_t smem = 0;
-  const int staged = 0;
   auto kern = k_rhs<MAXS>;
   const int threads = 128;
+  size_t smem = 0;
+  const int staged = stage_pays(hm, kern, threads, &smem);
   int64_t want = (n + threads - 1) / threads;
   int64_t cap = blocks_for(kern, threads, smem);
   int blocks = (int)(want < cap ? want : cap);
@@ -347,12 +367,10 @@ static cudaError_t rkf45_impl(const HostMech& hm, int64_t n, const double* p, do
                               const double* dt, double* h_io, const SolverParams& sp,
                               int32_t* steps, int32_t* status, int32_t* queue, cudaStream_t st,
                               const LaunchCfg& cfg) {
-  size_t smem = 0;
-  const int staged = stage_fits(hm, &smem) ? 1 : 0;
-  if (!staged) smem = 0;
   auto kern = k_rkf45<MAXS>;
-  if (smem > 48 * 1024) cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   const int threads = 128;
+  size_t smem = 0;
+  const int staged = stage_pays(hm, kern, threads, &smem);
   int64_t want = (n + threads - 1) / threads;
   int64_t cap = blocks_for(kern, threads, smem);
   if (cfg.ctas_per_sm > 0) cap = (int64_t)cfg.ctas_per_sm * sm_count();
