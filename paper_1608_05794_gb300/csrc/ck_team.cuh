@@ -504,10 +504,12 @@ static __device__ void team_jacobian(const DevMech& m, const double* tab, double
 // column kq = k / G, position kt = k % G):
 //   1. the owners of column k pick the pivot among rows i >= k (magnitudes
 //      compared as integers: the bit pattern of |v| orders like |v|, NaN
-//      above +inf; ties take the smallest row) with shuffles inside their
-//      group, form 1 / pivot, and write the column below the diagonal, as it
-//      stands after the exchange of rows k and p (row p takes row k's
-//      entry), to lb; their whole warp scales it into the multipliers;
+//      above +inf; ties take the smallest row) with shuffles of (magnitude,
+//      row) inside their group, fetch the pivot's value from the lane that
+//      holds its row, form 1 / pivot, and write the column below the
+//      diagonal, as it stands after the exchange of rows k and p (row p
+//      takes row k's entry), to lb; their whole warp scales it into the
+//      multipliers;
 //   2. barrier; the owners of rows k and p exchange the two rows through
 //      shared memory, which also publishes the new row k (the pivot row) in
 //      ub; barrier;
@@ -597,7 +599,7 @@ __device__ __forceinline__ int lu_pivot(const F (&a)[T][T], int n, int kt, F* sc
     const int i = tr + G * r;
     const bool ok = (r > KQ || tr >= kt) && i < n;
     const unsigned long long key = abs_key(a[r][KQ]);
-    const bool take = ok && (bi == n || key > best);
+    const bool take = ok && key > best;
     best = take ? key : best;
     bv = take ? a[r][KQ] : bv;
     bi = take ? i : bi;
@@ -605,15 +607,14 @@ __device__ __forceinline__ int lu_pivot(const F (&a)[T][T], int n, int kt, F* sc
 #pragma unroll
   for (int off = 1; off < G; off <<= 1) {
     const unsigned long long ok_ = __shfl_xor_sync(0xffffffffu, best, off, G);
-    const F ov = __shfl_xor_sync(0xffffffffu, bv, off, G);
     const int oi = __shfl_xor_sync(0xffffffffu, bi, off, G);
-    const bool take = oi < n && (bi == n || ok_ > best || (ok_ == best && oi < bi));
+    const bool take = ok_ > best || (ok_ == best && oi < bi);
     best = take ? ok_ : best;
-    bv = take ? ov : bv;
     bi = take ? oi : bi;
   }
   const int p = bi;
   const bool sing = p >= n || best == 0 || best >= INFB;
+  bv = __shfl_sync(0xffffffffu, bv, p % G, G);  // the value from the lane that holds row p
   const F akk = __shfl_sync(0xffffffffu, a[KQ][KQ], kt, G);
   ip = rcp_rn(sing ? F(1) : bv);
   if (tc == kt && !sing) {
@@ -686,7 +687,7 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
         const int i = tr + G * r;
         const bool ok = (r > KQ || tr >= kt) && i < n;
         const unsigned long long key = abs_key(a[r][KQ]);
-        if (ok && (bi == n || key > best)) {
+        if (ok && key > best) {
           best = key;
           bv = a[r][KQ];
           bi = i;
@@ -695,16 +696,15 @@ __device__ __forceinline__ bool lu_step(F (&a)[T][T], int n, int kt, int* piv, F
 #pragma unroll
       for (int off = 1; off < G; off <<= 1) {
         const unsigned long long ok_ = __shfl_xor_sync(gmask, best, off, G);
-        const F ov = __shfl_xor_sync(gmask, bv, off, G);
         const int oi = __shfl_xor_sync(gmask, bi, off, G);
-        if (oi < n && (bi == n || ok_ > best || (ok_ == best && oi < bi))) {
+        if (ok_ > best || (ok_ == best && oi < bi)) {
           best = ok_;
-          bv = ov;
           bi = oi;
         }
       }
       const int p = bi;
       sing = p >= n || best == 0 || best >= INFB;
+      bv = __shfl_sync(gmask, bv, p % G, G);  // the value from the lane that holds row p
       // column k as it stands after the exchange: row p takes row k's entry
       const F akk = __shfl_sync(gmask, a[KQ][KQ], kt, G);
       if (!sing) {

@@ -140,6 +140,63 @@ def test_lu_reports_singular(ck):
     assert piv.cpu().numpy()[1, 0] == 1
 
 
+@pytest.mark.parametrize("dim,k,rows", [(8, 0, (3, 5)), (11, 2, (9, 4, 6)), (54, 30, (43, 35, 38)),
+                                         (54, 47, (53, 50)), (112, 0, (17, 97, 33)), (112, 64, (96, 81, 80))])
+def test_lu_pivot_ties_take_the_first_row(ck, oracle_lib, dim, k, rows):
+    # upper triangular in the columns before k, so steps 0..k-1 exchange
+    # nothing and leave column k exactly as given; there the rows `rows`
+    # share the largest magnitude (signs mixed), and the smallest of them
+    # must become pivot k, as in the oracle, whichever lanes, tile slots and
+    # warps hold them
+    rng = np.random.default_rng(dim * 1000 + k)
+    A = np.triu(rng.standard_normal((dim, dim))) + 4.0 * np.eye(dim)
+    A[k + 1:, k] = rng.uniform(-1.0, 1.0, size=dim - k - 1)
+    A[k, k] = 0.5
+    for q, i in enumerate(rows):
+        A[i, k] = 6.0 if q % 2 == 0 else -6.0
+    a_d = _dev(A[None])
+    piv = torch.empty((1, dim), dtype=torch.int32, device="cuda")
+    info = torch.empty(1, dtype=torch.int32, device="cuda")
+    ck.lu_factor(a_d, piv, info)
+    torch.cuda.synchronize()
+    _, piv_o, info_o = oracle_lib.lu_factor(A)
+    P = piv.cpu().numpy()[0]
+    assert info.cpu().tolist() == [0] and info_o == 0
+    assert P[k] == min(rows) == piv_o[k]
+    assert np.array_equal(P[:k], np.arange(k))
+
+
+@pytest.mark.parametrize("dim,zero_at", [(54, 0), (54, 30), (112, 70), (11, 10)])
+def test_lu_reports_a_late_singular_pivot(ck, dim, zero_at):
+    # upper triangular: no row exchanges, and the column below a zero
+    # diagonal entry is zero, so pivot zero_at is the first zero one
+    rng = np.random.default_rng(dim + zero_at)
+    A = np.triu(rng.standard_normal((dim, dim))) + 4.0 * np.eye(dim)
+    A[zero_at, zero_at] = 0.0
+    a_d = _dev(A[None])
+    piv = torch.empty((1, dim), dtype=torch.int32, device="cuda")
+    info = torch.empty(1, dtype=torch.int32, device="cuda")
+    ck.lu_factor(a_d, piv, info)
+    torch.cuda.synchronize()
+    assert info.cpu().tolist() == [zero_at + 1]
+    assert np.array_equal(piv.cpu().numpy()[0, :zero_at], np.arange(zero_at))
+
+
+@pytest.mark.parametrize("dim", [11, 54, 112])
+def test_lu_reports_non_finite_matrices(ck, dim):
+    rng = np.random.default_rng(dim)
+    A = rng.standard_normal((3, dim, dim)) + 4.0 * np.eye(dim)
+    A[0, dim // 2, dim // 3] = np.nan
+    A[1, dim - 1, 0] = np.inf
+    a_d = _dev(A)
+    piv = torch.empty((3, dim), dtype=torch.int32, device="cuda")
+    info = torch.empty(3, dtype=torch.int32, device="cuda")
+    ck.lu_factor(a_d, piv, info)
+    torch.cuda.synchronize()
+    I = info.cpu().tolist()
+    assert I[0] != 0 and I[1] != 0 and I[2] == 0
+
+
 def _integrate_gpu(ck, gm, method, p, y, dt, **kw):
     yd = _dev(y)
     st = torch.empty(y.shape[0], dtype=torch.int32, device="cuda")
