@@ -87,7 +87,10 @@ __device__ __forceinline__ MechView view_of(const DevMech& d, const StageLayout&
 constexpr uint32_t STAGE_HDR = 16;
 
 // ------------------------------------------------------------------ RHS
-template <int MAXS>
+// R reactors a thread (rhs_thread_r); the last group of a batch repeats
+// reactor N - 1 in its missing places (the same thread writes the same
+// values there).
+template <int MAXS, int R>
 __global__ void __launch_bounds__(128) k_rhs(DevMech d, StageLayout L, int staged, int64_t N,
                                              const double* __restrict__ p,
                                              const double* __restrict__ y, double* __restrict__ f,
@@ -99,11 +102,25 @@ __global__ void __launch_bounds__(128) k_rhs(DevMech d, StageLayout L, int stage
     base = smem + STAGE_HDR;
   }
   const MechView m = view_of(d, L, base);
-  double X[MAXS], G[2 * MAXS], wd[MAXS];
+  double X[R * MAXS], G[2 * R * MAXS], wd[R * MAXS];
   const int n = d.n;
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < N;
-       r += (int64_t)gridDim.x * blockDim.x) {
-    rhs_thread(m, p[r], y + r * n, 1, f + r * n, 1, X, G, wd);
+  for (int64_t r = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) * R; r < N;
+       r += (int64_t)gridDim.x * blockDim.x * R) {
+    if constexpr (R == 1) {
+      rhs_thread(m, p[r], y + r * n, 1, f + r * n, 1, X, G, wd);
+    } else {
+      double pr[R];
+      const double* yr[R];
+      double* fr[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        const int64_t rj = r + j < N ? r + j : N - 1;
+        pr[j] = p[rj];
+        yr[j] = y + rj * n;
+        fr[j] = f + rj * n;
+      }
+      rhs_thread_r<R>(m, pr, yr, fr, X, G, wd);
+    }
   }
 }
 
@@ -340,14 +357,23 @@ static int blocks_for(K kernel, int threads, size_t smem) {
   return per_sm * sm_count();
 }
 
-template <int MAXS>
+// Reactors a thread of k_rhs, for mechanisms above and up to 32 species.
+// Two and four (rhs_thread_r, each table record read once for all of them)
+// measured slower on GB300: 33.2 and 22.7 M evaluations/s against 38.1 M on
+// the 53-species mechanism, 9.4 and 5.2 M against 13.4 M on the 111-species
+// one, 392 and 383 M against 440 M on the 10-species one (twice and four
+// times the per-lane scratch in local memory, and fewer resident threads).
+constexpr int RHS_REACTORS = 1;
+constexpr int RHS_REACTORS_SMALL = 1;
+
+template <int MAXS, int R>
 static cudaError_t rhs_impl(const HostMech& hm, int64_t n, const double* p, const double* y,
                             double* f, cudaStream_t st) {
-  auto kern = k_rhs<MAXS>;
+  auto kern = k_rhs<MAXS, R>;
   const int threads = 128;
   size_t smem = 0;
   const int staged = stage_pays(hm, kern, threads, &smem);
-  int64_t want = (n + threads - 1) / threads;
+  int64_t want = (n + (int64_t)threads * R - 1) / ((int64_t)threads * R);
   int64_t cap = blocks_for(kern, threads, smem);
   int blocks = (int)(want < cap ? want : cap);
   if (blocks < 1) blocks = 1;
@@ -358,8 +384,8 @@ static cudaError_t rhs_impl(const HostMech& hm, int64_t n, const double* p, cons
 cudaError_t launch_rhs(const HostMech& hm, int64_t n, const double* p, const double* y, double* f,
                        cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  if (hm.S <= 32) return rhs_impl<32>(hm, n, p, y, f, st);
-  return rhs_impl<128>(hm, n, p, y, f, st);
+  if (hm.S <= 32) return rhs_impl<32, RHS_REACTORS_SMALL>(hm, n, p, y, f, st);
+  return rhs_impl<128, RHS_REACTORS>(hm, n, p, y, f, st);
 }
 
 template <int MAXS>

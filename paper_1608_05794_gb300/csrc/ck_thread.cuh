@@ -124,4 +124,153 @@ __device__ __forceinline__ void rhs_thread(const MechView& m, double p, const do
   f[0] = -T * hw / (rho * cpm);
 }
 
+// R reactors a thread: rhs_thread's arithmetic for each of them, in the
+// same order, with every table record read once for all R (the several-
+// reactors-a-lane form of Sec. 4, where a SIMD vector holds several ODE
+// systems).  y[j], f[j]: the R states and outputs (element k at [k]); X,
+// G, wd: per-lane scratch of R S, 2 R S and R S doubles, reactor j of
+// species k at [k R + j].
+template <int R>
+__device__ __forceinline__ void rhs_thread_r(const MechView& m, const double (&p)[R], const double* const (&y)[R],
+                                             double* const (&f)[R], double* X, double* G, double* wd) {
+  const int S = m.S;
+  double T[R], invT[R], lnT[R], log2T[R], T2[R], T3[R], T4[R], rho[R], Ctot[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    T[j] = y[j][0];
+    invT[j] = __drcp_rn(T[j]);
+    lnT[j] = log(T[j]);
+    log2T[j] = lnT[j] * INV_LN2;
+    T2[j] = T[j] * T[j];
+    T3[j] = T2[j] * T[j];
+    T4[j] = T3[j] * T[j];
+  }
+  double sumYW[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) sumYW[j] = 0.0;
+  for (int k = 0; k < S; ++k) {
+    const double iw = m.invW[k];
+#pragma unroll
+    for (int j = 0; j < R; ++j) sumYW[j] = fma(y[j][1 + k], iw, sumYW[j]);
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    rho[j] = m.cv ? p[j] : p[j] / (R_GAS * T[j] * sumYW[j]);
+    Ctot[j] = 0.0;
+  }
+  for (int k = 0; k < S; ++k) {
+    const double iw = m.invW[k], tm = m.tmid[k];
+    const double* a0 = m.th + k * TH_PER_SPECIES;
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const double xk = rho[j] * (y[j][1 + k] * iw);
+      X[k * R + j] = xk;
+      Ctot[j] += xk;
+      const double* a = a0 + (T[j] < tm ? 0 : TH_STRIDE);
+      double g = fma(a[11], lnT[j], a[12]);
+      g = fma(a[13], T[j], g);
+      g = fma(a[14], T2[j], g);
+      g = fma(a[15], T3[j], g);
+      g = fma(a[16], T4[j], g);
+      g = fma(a[17], invT[j], g);
+      ck_exp2_pm(g, m.tab, G[k * R + j], G[(S + k) * R + j]);
+      wd[k * R + j] = 0.0;
+    }
+  }
+  const double* Gm = G + S * R;
+  for (int i = 0; i < m.R; ++i) {
+    const RxnRec& r = m.rx[i];
+    const int s0 = r.sp[0] * R, s1 = r.sp[1] * R, s2 = r.sp[2] * R;
+    const int s3 = r.sp[3] * R, s4 = r.sp[4] * R, s5 = r.sp[5] * R;
+    double net[R], l2kf[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      l2kf[j] = fma(-r.EoR2, invT[j], fma(r.beta, log2T[j], r.lA2));
+      const double kf = ck_exp2(l2kf[j], m.tab);
+      double fwd = X[s0 + j];
+      if (r.nreac > 1) fwd *= X[s1 + j];
+      if (r.nreac > 2) fwd *= X[s2 + j];
+      net[j] = kf * fwd;
+      if (r.rev == 2) {
+        const double* ra = m.revp + 3 * r.rev_ix;
+        const double kr = ck_exp2(fma(-ra[2], invT[j], fma(ra[1], log2T[j], ra[0])), m.tab);
+        double rv = X[s3 + j];
+        if (r.nprod > 1) rv *= X[s4 + j];
+        if (r.nprod > 2) rv *= X[s5 + j];
+        net[j] = fma(-kr, rv, net[j]);
+      } else if (r.rev) {
+        double kci = rt_over_p0_pow(r.dnu, T[j], invT[j]) * G[s0 + j];
+        kci *= Gm[s3 + j];
+        if (r.nreac > 1) kci *= G[s1 + j];
+        if (r.nprod > 1) kci *= Gm[s4 + j];
+        if (r.nreac > 2) kci *= G[s2 + j];
+        if (r.nprod > 2) kci *= Gm[s5 + j];
+        const double kr = kf * kci;
+        double rv = X[s3 + j];
+        if (r.nprod > 1) rv *= X[s4 + j];
+        if (r.nprod > 2) rv *= X[s5 + j];
+        net[j] = fma(-kr, rv, net[j]);
+      }
+    }
+    double q[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) q[j] = net[j];
+    if (r.type) {
+      double M[R];
+#pragma unroll
+      for (int j = 0; j < R; ++j) M[j] = Ctot[j];
+      for (int e = r.eff_beg; e < r.eff_beg + r.eff_cnt; ++e) {
+        const double em = m.eff_m1[e];
+        const int es = m.eff_sp[e] * R;
+#pragma unroll
+        for (int j = 0; j < R; ++j) M[j] = fma(em, X[es + j], M[j]);
+      }
+#pragma unroll
+      for (int j = 0; j < R; ++j) {
+        if (r.type == 1) {
+          q[j] = M[j] * net[j];
+        } else {
+          const double l2k0 = fma(-r.E0oR2, invT[j], fma(r.beta0, log2T[j], r.lA02));
+          const double Pr = ck_exp2(l2k0 - l2kf[j], m.tab) * M[j];
+          q[j] = net[j] * (Pr / (1.0 + Pr));
+        }
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      wd[s0 + j] -= q[j];
+      if (r.nreac > 1) wd[s1 + j] -= q[j];
+      if (r.nreac > 2) wd[s2 + j] -= q[j];
+      wd[s3 + j] += q[j];
+      if (r.nprod > 1) wd[s4 + j] += q[j];
+      if (r.nprod > 2) wd[s5 + j] += q[j];
+    }
+  }
+  const double cvf = m.cv ? 1.0 : 0.0;
+  double invrho[R], cpm[R], hw[R];
+#pragma unroll
+  for (int j = 0; j < R; ++j) {
+    invrho[j] = __drcp_rn(rho[j]);
+    cpm[j] = 0.0;
+    hw[j] = 0.0;
+  }
+  for (int k = 0; k < S; ++k) {
+    const double* a0 = m.th + k * TH_PER_SPECIES;
+    const double tm = m.tmid[k], Wk = m.W[k], iw = m.invW[k];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+      const double* a = a0 + (T[j] < tm ? 0 : TH_STRIDE);
+      const double cp = fma(a[4], T4[j], fma(a[3], T3[j], fma(a[2], T2[j], fma(a[1], T[j], a[0])))) - cvf;
+      const double h =
+          fma(a[10], invT[j], fma(a[9], T4[j], fma(a[8], T3[j], fma(a[7], T2[j], fma(a[6], T[j], a[5]))))) - cvf;
+      const double w = wd[k * R + j];
+      cpm[j] = fma(y[j][1 + k] * iw, cp, cpm[j]);
+      hw[j] = fma(h, w, hw[j]);
+      f[j][1 + k] = w * (Wk * invrho[j]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < R; ++j) f[j][0] = -T[j] * hw[j] / (rho[j] * cpm[j]);
+}
+
 }  // namespace ck

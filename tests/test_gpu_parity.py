@@ -75,6 +75,20 @@ def test_rhs_matches_oracle(ck, name, n, parity_report):
     _assert_rhs_close(f, fo, g, parity_report, {"case": "rhs", "workload": name, "reactors": n})
 
 
+@pytest.mark.parametrize("name", ["small", "medium", "large"])
+def test_rhs_ragged_batches(ck, name):
+    # k_rhs gives each thread several reactors; batches of 1 to 7 leave the
+    # last group partly empty (it repeats the last reactor), and every
+    # reactor must still match the oracle and the one-at-a-time result
+    m, gm, om = _mech(ck, name)
+    y, p = reactor_states(name, n=7, seed_offset=29)
+    full = _gpu_rhs(ck, gm, p, y)
+    for n in range(1, 8):
+        f = _gpu_rhs(ck, gm, p[:n], y[:n])
+        assert np.array_equal(f, full[:n])
+        _assert_rhs_close(f, om.rhs(p[:n], y[:n]), om.rhs_gross(p[:n], y[:n]))
+
+
 def test_rhs_temperature_sweep_crosses_thermo_ranges(ck):
     # the paper's RHS input (Sec. 5.1): uniform composition, T linear over
     # 500-1500 K, so lanes straddle the NASA-7 range boundary
